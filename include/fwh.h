@@ -1,0 +1,182 @@
+/*
+ * fwh.h -- C ABI of the GB300 FW-H library (permeable-surface, nondimensional,
+ * wind-tunnel Ffowcs Williams-Hawkings integral of OpenCFD-FWH,
+ * arXiv 2312.16263).
+ *
+ * The library evaluates, for every (surface panel, source time, observer),
+ * the Farassat-1A-type thickness and loading integrands of the wind-tunnel
+ * form (Sec. II C, Eqs. pT_WT and pL_WT, nondimensionalised as Eqs. pT_WT_nd
+ * and pL_WT_nd of Sec. II D), with the convected distance from the Garrick
+ * triangle and the angle of attack by rotation (Eqs. R_New .. R2_New), and
+ * places each subface's source-time signal on the observer-time grid by
+ * natural cubic-spline interpolation (Sec. III B, "interp pressure signal"),
+ * summed over subfaces (Sec. III C).
+ *
+ * Conventions for every entry point:
+ *  - Everything is nondimensional (Sec. II D): rho* = rho/rho0,
+ *    u* = u/U0, p* = p/(rho0 U0^2), c0* = 1/M0, x* = x/Lref, t* = t U0/Lref.
+ *  - Fields are PULSATIONS, laid out [nt][5][P]: for frame i and panel p,
+ *    fields[(i*5 + c)*P + p] holds c = 0 rho', 1 u', 2 v', 3 w', 4 p'.
+ *    Totals are rebuilt as rho = 1 + rho', u = (cos a, sin a, 0) + u'.
+ *    FWH_FP64 handles take double fields, FWH_MIXED handles float fields.
+ *  - Source time tau_i = i dt, i = 0..nt-1.  Observer o's time grid is
+ *    t_j = t_start(o) + j dt with t_start = M0 R_max(o) (Eq. t_start) and
+ *    N_o = floor((t_end - t_start)/dt) + 1 valid bins, t_end = tau_max +
+ *    M0 R_min(o) (Eq. t_end).  Outputs are [O][nt] doubles, row o holding
+ *    p'(t_j) for j < N_o and 0 for j >= N_o.
+ *  - The caller owns every buffer it passes; the library copies geometry and
+ *    observers into its own device memory.  Buffers may be device pointers
+ *    (used in place, on `stream`) or host pointers (pageable or pinned; the
+ *    library stages them through device memory it owns and copies results
+ *    back before returning).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = default stream).
+ *    Device work is enqueued on it; calls with host outputs synchronise it.
+ *  - Every call returns a status and never aborts; fwh_last_error() gives a
+ *    message for the last failing call on that handle.
+ */
+#ifndef FWH_H_
+#define FWH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fwh_ctx *fwh_handle;
+
+typedef enum {
+  FWH_OK = 0,
+  FWH_ERR_ARG = 1,     /* invalid argument (sizes, ranges, null pointers) */
+  FWH_ERR_CUDA = 2,    /* a CUDA runtime call or kernel launch failed */
+  FWH_ERR_OOM = 3,     /* device or host allocation failed */
+  FWH_ERR_STATE = 4,   /* call out of order (e.g. forward before observers) */
+  FWH_ERR_TIMEOUT = 5  /* a bounded device-side wait gave up */
+} fwh_status;
+
+enum { FWH_FP64 = 0, FWH_MIXED = 1 };
+
+/*
+ * Create a handle for one permeable surface of n_panels subfaces
+ * (the FWH_Surface_Geo.dat content of App. A2, as arrays):
+ *   centroids [P][3]  subface centres y_i (double, row-major)
+ *   normals   [P][3]  unit outward normals n_i (|n| = 1 within 1e-6)
+ *   areas     [P]     subface areas dS (> 0)
+ * mach  M0 = U0/c0 in (0, 1) (Eq. M0), aoa_rad the angle of attack in the
+ * x-y plane (Eqs. d1_prime, d2_prime), c0 the nondimensional sound speed,
+ * which must equal 1/M0 within 1e-12 relative (Sec. II D), dt > 0 the
+ * nondimensional sampling interval, precision FWH_FP64 or FWH_MIXED
+ * (mixed: FP32 fields and integrand arithmetic, FP64 arrival times and
+ * interpolation weights, compensated per-bin accumulation, FP64 output).
+ * Errors: FWH_ERR_ARG on any invalid value (no handle is created),
+ * FWH_ERR_OOM / FWH_ERR_CUDA on allocation or device failure.
+ */
+fwh_status fwh_create(fwh_handle *out, int64_t n_panels, const double *centroids,
+                      const double *normals, const double *areas, double mach,
+                      double aoa_rad, double c0, double dt, int precision);
+
+/*
+ * Set the observers (observers.dat of Sec. III A): xyz [O][3] doubles, host
+ * or device.  Computes, once per geometry, the convected distance R and unit
+ * radiation vector R-hat of every (panel, observer) pair (Eqs. R_New ..
+ * R2_New), the per-observer R_max/R_min (the reductions the paper performs
+ * with MPI_ALLREDUCE, Sec. III B "compute t"), the integrand coefficients of
+ * Eqs. pT_WT_nd / pL_WT_nd and the arrival-time shift and spline weights, all
+ * in FP64.  May be called again to replace the observer set.
+ * Errors: FWH_ERR_ARG (n_obs < 1, null xyz, non-finite values).
+ */
+fwh_status fwh_set_observers(fwh_handle h, int64_t n_obs, const double *xyz);
+
+/*
+ * Forward pass: far-field pressure p_out [O][nt] (double) from the fields
+ * [nt][5][P] (double for FWH_FP64, float for FWH_MIXED), nt >= 3.
+ * Covers the "compute Noise", "compute t", "interp pressure signal" and
+ * surface-integration stages (Sec. III B, III C).
+ * Errors: FWH_ERR_STATE before fwh_set_observers, FWH_ERR_ARG for nt < 3 or
+ * null pointers, FWH_ERR_CUDA / FWH_ERR_OOM on device failure.
+ */
+fwh_status fwh_forward(fwh_handle h, const void *fields, int64_t nt, double *p_out,
+                       void *stream);
+
+/*
+ * Observer window for a record of nt frames: t_start [O] (Eq. t_start) and
+ * n_valid [O] = N_o (from Eq. t_end).  Host pointers.
+ */
+fwh_status fwh_observer_window(fwh_handle h, int64_t nt, double *t_start,
+                               int64_t *n_valid);
+
+/*
+ * Adjoint: given grad_p = dLoss/dp_out [O][nt] (double; entries j >= N_o are
+ * ignored), write grad_fields = dLoss/dfields [nt][5][P] (same type as the
+ * fields).  It is the exact transpose of fwh_forward's linear stages (spline
+ * interpolation, finite differences, integrand coefficients) followed by the
+ * Jacobian of the integrands of Eqs. Qn_New_nd / Li_New_nd at `fields`,
+ * computed as a gather over observers (no atomics on the gradient).
+ * Errors: as fwh_forward.
+ */
+fwh_status fwh_backward(fwh_handle h, const void *fields, int64_t nt,
+                        const double *grad_p, void *grad_fields, void *stream);
+
+/*
+ * Batched forward over n handles (several uneven surfaces, each with its own
+ * observers, fields, nt and p_out), run by one persistent work-queue kernel
+ * per time segment; all handles must share one precision.  With device
+ * buffers the launch sequence is captured once in a CUDA graph keyed on the
+ * handle set and replayed on later calls with the same arguments.
+ * Errors: FWH_ERR_ARG (n < 1, mixed precisions, null entries),
+ * FWH_ERR_STATE (a handle without observers), FWH_ERR_CUDA.
+ */
+fwh_status fwh_batch_forward(int n, const fwh_handle *hs, const void *const *fields,
+                             const int64_t *nt, double *const *p_out, void *stream);
+
+/*
+ * Autotune: time the candidate tile shapes of the forward kernel on this
+ * handle's geometry for a record of nt frames (synthetic zero fields; the
+ * caller's data are not touched) and keep the fastest for later calls.
+ * Writes the chosen configuration index to *chosen (may be NULL).
+ */
+fwh_status fwh_autotune(fwh_handle h, int64_t nt, int *chosen, void *stream);
+
+/*
+ * Force a forward tile configuration (index into the candidate table; -1
+ * restores the default).  For benchmarking and tests.
+ */
+fwh_status fwh_set_tile_config(fwh_handle h, int config);
+
+/*
+ * Device times (milliseconds, CUDA events on the launching stream) of the
+ * last fwh_forward on this handle: [0] integrand preparation, [1] the
+ * forward scatter kernel, [2] the whole call.  Recording is enabled by
+ * fwh_set_timing(h, 1) and costs two event records per kernel.
+ */
+fwh_status fwh_set_timing(fwh_handle h, int enable);
+fwh_status fwh_last_timings(fwh_handle h, float *ms3);
+
+/*
+ * Synchronise `stream` and report the device-side checks raised by this
+ * handle's kernels since the last check (a panel set whose arrival spread
+ * exceeded its window -> FWH_ERR_CUDA; a bounded wait that gave up ->
+ * FWH_ERR_TIMEOUT).  Calls with host outputs run this check themselves.
+ */
+fwh_status fwh_check(fwh_handle h, void *stream);
+
+/* Number of panels, observers and the precision of a handle. */
+fwh_status fwh_get_sizes(fwh_handle h, int64_t *n_panels, int64_t *n_obs,
+                         int *precision);
+
+/* Destroy a handle and free its device memory (NULL is ignored). */
+void fwh_destroy(fwh_handle h);
+
+/* Message of the last failing call on h ("" if none); h may be NULL for
+ * errors of fwh_create. The pointer stays valid until the next call. */
+const char *fwh_last_error(fwh_handle h);
+
+/* Library version string. */
+const char *fwh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FWH_H_ */

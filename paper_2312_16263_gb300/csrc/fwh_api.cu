@@ -1,0 +1,864 @@
+// C ABI of the GB300 FW-H library: handles, the host planner, workspace,
+// host/device staging, launches, timing and the batched graph path.
+//
+// Planner.  Panels are visited in the caller's order when that order is
+// spatially coherent, else in Morton (Z-curve) order of their centroids.
+// They are grouped into "panel sets" of up to kMaxSet consecutive panels
+// whose arrival shifts, for every observer, span at most S samples, where
+//   |i0(p1, o) - i0(p2, o)| <= M0 |R(p1, o) - R(p2, o)| / dt + 1
+//                          <= M0 |y1 - y2| / ((1 - M0) dt) + 1
+// because |grad_y R| = R / R* <= 1 / (1 - M0) (R, R* of Eqs. R_New,
+// R_s_New).  The set's bounding-box diagonal bounds |y1 - y2|, so the bound
+// needs no per-observer data and holds for any observer set.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/fwh.h"
+#include "fwh_internal.cuh"
+
+using namespace fwh;
+
+namespace {
+
+constexpr int kMaxSet = 64;
+
+struct Buf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uintptr_t> key;
+};
+
+// Device-side argument table of one batched launch (lives with its graph).
+struct BatchPlan {
+  Buf args, prefix, counter;
+  int total = 0, ctas = 0, cfg = 0;
+};
+
+}  // namespace
+
+struct fwh_ctx {
+  int64_t P = 0, O = 0;
+  double mach = 0, aoa = 0, dt = 0, ca = 1, sa = 0;
+  int precision = FWH_FP64;
+  std::vector<double> y, n, dS;  // library (planner) order
+  std::vector<int> perm;          // library position -> caller index
+  bool identity = true;
+  std::vector<double> xobs;
+  std::vector<double> Rmax, Rmin;
+  // device state
+  double *d_y = nullptr, *d_n = nullptr, *d_dS = nullptr, *d_x = nullptr;
+  double *d_Rmax = nullptr, *d_Rmin = nullptr;
+  int *d_perm = nullptr, *d_err = nullptr;
+  Buf coef, X, G, nvalid, sets, stage_in, stage_out, stage_grad;
+  // per-nt
+  int64_t nt = -1;
+  int ntp = 0;
+  std::vector<int> h_nvalid;
+  std::vector<double> h_tstart;
+  // planner
+  int plan_win = -1, plan_ch = -1;
+  std::vector<int> set_begin;
+  int cfg = -1;  // forced/tuned forward config (-1 default)
+  bool timing = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  float last_ms[3] = {0, 0, 0};
+  std::string err;
+  // batch
+  std::map<std::vector<uintptr_t>, Graph> graphs;
+  std::map<std::vector<uintptr_t>, BatchPlan> bplans;
+  cudaStream_t side = nullptr;
+  cudaEvent_t bev[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_err;  // errors without a handle
+
+fwh_status fail(fwh_handle h, fwh_status st, const std::string &msg) {
+  if (h) {
+    h->err = msg;
+  } else {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_err = msg;
+  }
+  return st;
+}
+
+fwh_status cuda_fail(fwh_handle h, cudaError_t e, const char *what) {
+  return fail(h, e == cudaErrorMemoryAllocation ? FWH_ERR_OOM : FWH_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, expr)                                   \
+  do {                                                \
+    cudaError_t e_ = (expr);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #expr); \
+  } while (0)
+
+cudaError_t ensure(Buf &b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (bytes == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e == cudaSuccess) b.bytes = bytes;
+  return e;
+}
+
+void release(Buf &b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t tsize(int precision) { return precision == FWH_FP64 ? sizeof(double) : sizeof(float); }
+
+uint64_t spread_bits(uint64_t v) {  // 21-bit -> every third bit
+  v &= 0x1fffff;
+  v = (v | v << 32) & 0x1f00000000ffffULL;
+  v = (v | v << 16) & 0x1f0000ff0000ffULL;
+  v = (v | v << 8) & 0x100f00f00f00f00fULL;
+  v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+  v = (v | v << 2) & 0x1249249249249249ULL;
+  return v;
+}
+
+// Greedy panel sets over `order`; returns set boundaries (positions).
+std::vector<int> build_sets(const std::vector<double> &y, int64_t P, double mach, double dt,
+                            int smax) {
+  const double k = mach / ((1.0 - mach) * dt);
+  std::vector<int> b{0};
+  double lo[3], hi[3];
+  int cnt = 0;
+  for (int64_t p = 0; p < P; ++p) {
+    const double *q = &y[3 * p];
+    if (cnt == 0) {
+      for (int c = 0; c < 3; ++c) lo[c] = hi[c] = q[c];
+      cnt = 1;
+      continue;
+    }
+    double nlo[3], nhi[3], d2 = 0;
+    for (int c = 0; c < 3; ++c) {
+      nlo[c] = std::min(lo[c], q[c]);
+      nhi[c] = std::max(hi[c], q[c]);
+      d2 += (nhi[c] - nlo[c]) * (nhi[c] - nlo[c]);
+    }
+    const double bound = k * std::sqrt(d2) + 1.0;
+    if (cnt >= kMaxSet || bound > (double)smax) {
+      b.push_back((int)p);
+      for (int c = 0; c < 3; ++c) lo[c] = hi[c] = q[c];
+      cnt = 1;
+    } else {
+      std::memcpy(lo, nlo, sizeof lo);
+      std::memcpy(hi, nhi, sizeof hi);
+      ++cnt;
+    }
+  }
+  b.push_back((int)P);
+  return b;
+}
+
+int default_cfg(const fwh_ctx *h) {
+  (void)h;
+  return 0;
+}
+
+// Observer tiling for a config: observers per warp and groups.
+void obs_tiling(const fwh_ctx *h, const FwdConfig &c, int *obs_per_cta, int *groups) {
+  int opw = (int)std::min<int64_t>(c.obs_per_warp, (h->O + c.warps - 1) / c.warps);
+  if (opw < 1) opw = 1;
+  *obs_per_cta = opw * c.warps;
+  *groups = (int)((h->O + *obs_per_cta - 1) / *obs_per_cta);
+}
+
+fwh_status plan(fwh_handle h, const FwdConfig &c) {
+  const int ch = 32 * c.tk;
+  if (h->plan_win == c.win && h->plan_ch == ch) return FWH_OK;
+  const int smax = c.win - ch - 1;
+  h->set_begin = build_sets(h->y, h->P, h->mach, h->dt, smax);
+  h->plan_win = c.win;
+  h->plan_ch = ch;
+  const size_t bytes = h->set_begin.size() * sizeof(int);
+  CK(h, ensure(h->sets, bytes));
+  CK(h, cudaMemcpy(h->sets.p, h->set_begin.data(), bytes, cudaMemcpyHostToDevice));
+  return FWH_OK;
+}
+
+// Per-nt window and workspace.  ntp is a multiple of 128 (every chunk size).
+fwh_status prepare_nt(fwh_handle h, int64_t nt) {
+  if (h->nt != nt) {
+    h->h_nvalid.assign(h->O, 0);
+    h->h_tstart.assign(h->O, 0.0);
+    const double tau_max = (double)(nt - 1) * h->dt;
+    for (int64_t o = 0; o < h->O; ++o) {
+      const double ts = h->mach * h->Rmax[o];                // Eq. t_start
+      const double te = tau_max + h->mach * h->Rmin[o];      // Eq. t_end
+      double nv = std::floor((te - ts) / h->dt) + 1.0;
+      nv = std::max(0.0, std::min((double)nt, nv));
+      h->h_nvalid[o] = (int)nv;
+      h->h_tstart[o] = ts;
+    }
+    CK(h, ensure(h->nvalid, h->O * sizeof(int)));
+    CK(h, cudaMemcpy(h->nvalid.p, h->h_nvalid.data(), h->O * sizeof(int),
+                     cudaMemcpyHostToDevice));
+    h->nt = nt;
+    h->ntp = (int)((nt + 127) / 128 * 128);
+  }
+  const size_t ts = tsize(h->precision);
+  CK(h, ensure(h->X, (size_t)h->P * h->ntp * kRec * ts));
+  return FWH_OK;
+}
+
+template <typename T>
+fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStream_t s) {
+  const bool fp64 = sizeof(T) == 8;
+  const int cfg = h->cfg >= 0 ? h->cfg : default_cfg(h);
+  const FwdConfig c = fwd_config(fp64, cfg);
+  fwh_status st = plan(h, c);
+  if (st != FWH_OK) return st;
+  if (h->timing) CK(h, cudaEventRecord(h->ev[0], s));
+  CK(h, cudaMemsetAsync(d_pout, 0, (size_t)h->O * h->nt * sizeof(double), s));
+  PrepArgs<T> pa{};
+  pa.fields = d_fields;
+  pa.perm = h->identity ? nullptr : h->d_perm;
+  pa.n = h->d_n;
+  pa.X = reinterpret_cast<T *>(h->X.p);
+  pa.P = (int)h->P;
+  pa.nt = (int)h->nt;
+  pa.ntp = h->ntp;
+  pa.ca = h->ca;
+  pa.sa = h->sa;
+  pa.dt = h->dt;
+  CK(h, launch_prep<T>(pa, s));
+  if (h->timing) CK(h, cudaEventRecord(h->ev[1], s));
+  FwdArgs<T> fa{};
+  fa.X = pa.X;
+  fa.coef = reinterpret_cast<const T *>(h->coef.p);
+  fa.p_out = d_pout;
+  fa.n_valid = reinterpret_cast<const int *>(h->nvalid.p);
+  fa.set_begin = reinterpret_cast<const int *>(h->sets.p);
+  fa.err = h->d_err;
+  fa.nsets = (int)h->set_begin.size() - 1;
+  fa.O = (int)h->O;
+  fa.ntp = h->ntp;
+  fa.nt = (int)h->nt;
+  obs_tiling(h, c, &fa.obs_per_cta, &fa.n_obs_groups);
+  fa.seg_len = c.seg_chunks * 32 * c.tk;
+  fa.n_segs = (h->ntp + fa.seg_len - 1) / fa.seg_len;
+  fa.win = c.win;
+  CK(h, launch_forward<T>(fa, cfg, s));
+  if (h->timing) {
+    CK(h, cudaEventRecord(h->ev[2], s));
+    CK(h, cudaEventSynchronize(h->ev[2]));
+    cudaEventElapsedTime(&h->last_ms[0], h->ev[0], h->ev[1]);
+    cudaEventElapsedTime(&h->last_ms[1], h->ev[1], h->ev[2]);
+    cudaEventElapsedTime(&h->last_ms[2], h->ev[0], h->ev[2]);
+  }
+  return FWH_OK;
+}
+
+void drop_graphs(fwh_handle h) {
+  for (auto &kv : h->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  h->graphs.clear();
+  for (auto &kv : h->bplans) {
+    release(kv.second.args);
+    release(kv.second.prefix);
+    release(kv.second.counter);
+  }
+  h->bplans.clear();
+}
+
+fwh_status check_device_flag(fwh_handle h, cudaStream_t s) {
+  int flag = 0;
+  CK(h, cudaMemcpyAsync(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  if (flag) {
+    CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+    if (flag & kErrTimeout) return fail(h, FWH_ERR_TIMEOUT, "device wait timed out");
+    return fail(h, FWH_ERR_CUDA, "device check failed (flags " + std::to_string(flag) + ")");
+  }
+  return FWH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fwh_version(void) { return "fwh-gb300 1.0 (sm_103a)"; }
+
+const char *fwh_last_error(fwh_handle h) {
+  if (h) return h->err.c_str();
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  return g_err.c_str();
+}
+
+fwh_status fwh_create(fwh_handle *out, int64_t P, const double *centroids,
+                      const double *normals, const double *areas, double mach, double aoa,
+                      double c0, double dt, int precision) {
+  if (!out) return fail(nullptr, FWH_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (P < 1 || P > (int64_t)1 << 30) return fail(nullptr, FWH_ERR_ARG, "n_panels out of range");
+  if (!centroids || !normals || !areas)
+    return fail(nullptr, FWH_ERR_ARG, "geometry pointer is NULL");
+  if (!(mach > 0.0 && mach < 1.0)) return fail(nullptr, FWH_ERR_ARG, "mach must be in (0, 1)");
+  if (!(std::fabs(c0 * mach - 1.0) <= 1e-12))
+    return fail(nullptr, FWH_ERR_ARG, "c0 must equal 1/mach (nondimensional sound speed)");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, FWH_ERR_ARG, "dt must be > 0");
+  if (!std::isfinite(aoa)) return fail(nullptr, FWH_ERR_ARG, "aoa must be finite");
+  if (precision != FWH_FP64 && precision != FWH_MIXED)
+    return fail(nullptr, FWH_ERR_ARG, "precision must be FWH_FP64 or FWH_MIXED");
+  // geometry may be host or device memory
+  std::vector<double> y(3 * P), n(3 * P), dS(P);
+  auto fetch = [&](std::vector<double> &dst, const double *src, size_t cnt) -> bool {
+    if (is_device_ptr(src))
+      return cudaMemcpy(dst.data(), src, cnt * sizeof(double), cudaMemcpyDeviceToHost) ==
+             cudaSuccess;
+    std::memcpy(dst.data(), src, cnt * sizeof(double));
+    return true;
+  };
+  if (!fetch(y, centroids, 3 * P) || !fetch(n, normals, 3 * P) || !fetch(dS, areas, P))
+    return fail(nullptr, FWH_ERR_CUDA, "cannot read geometry");
+  for (int64_t p = 0; p < P; ++p) {
+    const double nn = n[3 * p] * n[3 * p] + n[3 * p + 1] * n[3 * p + 1] + n[3 * p + 2] * n[3 * p + 2];
+    if (!(std::fabs(std::sqrt(nn) - 1.0) <= 1e-6))
+      return fail(nullptr, FWH_ERR_ARG, "normal " + std::to_string(p) + " is not unit length");
+    if (!(dS[p] > 0.0) || !std::isfinite(dS[p]))
+      return fail(nullptr, FWH_ERR_ARG, "area " + std::to_string(p) + " must be > 0");
+    for (int c = 0; c < 3; ++c)
+      if (!std::isfinite(y[3 * p + c]))
+        return fail(nullptr, FWH_ERR_ARG, "centroid " + std::to_string(p) + " not finite");
+  }
+  fwh_ctx *h = new (std::nothrow) fwh_ctx();
+  if (!h) return fail(nullptr, FWH_ERR_OOM, "host allocation failed");
+  h->P = P;
+  h->mach = mach;
+  h->aoa = aoa;
+  h->dt = dt;
+  h->ca = std::cos(aoa);
+  h->sa = std::sin(aoa);
+  h->precision = precision;
+
+  // planner order: the caller's order unless a Morton order packs the
+  // arrival spreads much better (decided with the default window).
+  const FwdConfig c0cfg = fwd_config(precision == FWH_FP64, 0);
+  const int smax = c0cfg.win - 32 * c0cfg.tk - 1;
+  std::vector<int> sets_id = build_sets(y, P, mach, dt, smax);
+  const double avg_id = (double)P / (double)(sets_id.size() - 1);
+  std::vector<int> order(P);
+  std::iota(order.begin(), order.end(), 0);
+  if (avg_id < 24.0 && P > kMaxSet) {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t p = 0; p < P; ++p)
+      for (int c = 0; c < 3; ++c) {
+        lo[c] = std::min(lo[c], y[3 * p + c]);
+        hi[c] = std::max(hi[c], y[3 * p + c]);
+      }
+    double ext = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], 1e-300});
+    std::vector<uint64_t> key(P);
+    for (int64_t p = 0; p < P; ++p) {
+      uint64_t q[3];
+      for (int c = 0; c < 3; ++c)
+        q[c] = (uint64_t)std::min(2097151.0, std::floor((y[3 * p + c] - lo[c]) / ext * 2097151.0));
+      key[p] = spread_bits(q[0]) | spread_bits(q[1]) << 1 | spread_bits(q[2]) << 2;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
+    std::vector<double> ys(3 * P);
+    for (int64_t p = 0; p < P; ++p)
+      for (int c = 0; c < 3; ++c) ys[3 * p + c] = y[3 * order[p] + c];
+    std::vector<int> sets_m = build_sets(ys, P, mach, dt, smax);
+    const double avg_m = (double)P / (double)(sets_m.size() - 1);
+    if (avg_m < 1.5 * avg_id) std::iota(order.begin(), order.end(), 0);
+  }
+  h->perm = order;
+  h->identity = true;
+  for (int64_t p = 0; p < P; ++p) h->identity = h->identity && order[p] == p;
+  h->y.resize(3 * P);
+  h->n.resize(3 * P);
+  h->dS.resize(P);
+  for (int64_t p = 0; p < P; ++p) {
+    for (int c = 0; c < 3; ++c) {
+      h->y[3 * p + c] = y[3 * order[p] + c];
+      h->n[3 * p + c] = n[3 * order[p] + c];
+    }
+    h->dS[p] = dS[order[p]];
+  }
+  cudaError_t e;
+  if ((e = cudaMalloc(&h->d_y, 3 * P * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_n, 3 * P * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_dS, P * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_perm, P * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_err, sizeof(int))) != cudaSuccess ||
+      (e = cudaMemcpy(h->d_y, h->y.data(), 3 * P * sizeof(double), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(h->d_n, h->n.data(), 3 * P * sizeof(double), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(h->d_dS, h->dS.data(), P * sizeof(double), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(h->d_perm, h->perm.data(), P * sizeof(int), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemset(h->d_err, 0, sizeof(int))) != cudaSuccess ||
+      (e = upload_pivots(0)) != cudaSuccess) {
+    fwh_destroy(h);
+    return cuda_fail(nullptr, e, "fwh_create device setup");
+  }
+  for (int i = 0; i < 4; ++i)
+    if ((e = cudaEventCreate(&h->ev[i])) != cudaSuccess) {
+      fwh_destroy(h);
+      return cuda_fail(nullptr, e, "cudaEventCreate");
+    }
+  *out = h;
+  return FWH_OK;
+}
+
+fwh_status fwh_set_observers(fwh_handle h, int64_t O, const double *xyz) {
+  if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
+  if (O < 1 || O > 65535) return fail(h, FWH_ERR_ARG, "n_obs must be in [1, 65535]");
+  if (!xyz) return fail(h, FWH_ERR_ARG, "xyz is NULL");
+  std::vector<double> x(3 * O);
+  if (is_device_ptr(xyz)) {
+    CK(h, cudaMemcpy(x.data(), xyz, 3 * O * sizeof(double), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(x.data(), xyz, 3 * O * sizeof(double));
+  }
+  for (double v : x)
+    if (!std::isfinite(v)) return fail(h, FWH_ERR_ARG, "observer coordinates must be finite");
+  if (h->d_x) cudaFree(h->d_x);
+  h->d_x = nullptr;
+  if (h->d_Rmax) cudaFree(h->d_Rmax);
+  if (h->d_Rmin) cudaFree(h->d_Rmin);
+  h->d_Rmax = h->d_Rmin = nullptr;
+  h->O = 0;
+  CK(h, cudaMalloc(&h->d_x, 3 * O * sizeof(double)));
+  CK(h, cudaMalloc(&h->d_Rmax, O * sizeof(double)));
+  CK(h, cudaMalloc(&h->d_Rmin, O * sizeof(double)));
+  CK(h, cudaMemcpy(h->d_x, x.data(), 3 * O * sizeof(double), cudaMemcpyHostToDevice));
+  const size_t ts = tsize(h->precision);
+  CK(h, ensure(h->coef, (size_t)h->P * O * kRec * ts));
+  GeomArgs g{};
+  g.y = h->d_y;
+  g.n = h->d_n;
+  g.dS = h->d_dS;
+  g.x = h->d_x;
+  g.P = (int)h->P;
+  g.O = (int)O;
+  g.mach = h->mach;
+  g.ca = h->ca;
+  g.sa = h->sa;
+  g.dt = h->dt;
+  g.Rmax = h->d_Rmax;
+  g.Rmin = h->d_Rmin;
+  CK(h, launch_window(g, 0));
+  if (h->precision == FWH_FP64)
+    CK(h, launch_coef<double>(g, reinterpret_cast<double *>(h->coef.p), 0));
+  else
+    CK(h, launch_coef<float>(g, reinterpret_cast<float *>(h->coef.p), 0));
+  h->Rmax.resize(O);
+  h->Rmin.resize(O);
+  CK(h, cudaMemcpy(h->Rmax.data(), h->d_Rmax, O * sizeof(double), cudaMemcpyDeviceToHost));
+  CK(h, cudaMemcpy(h->Rmin.data(), h->d_Rmin, O * sizeof(double), cudaMemcpyDeviceToHost));
+  h->xobs = x;
+  h->O = O;
+  h->nt = -1;  // window depends on the observers
+  drop_graphs(h);
+  return FWH_OK;
+}
+
+fwh_status fwh_observer_window(fwh_handle h, int64_t nt, double *t_start, int64_t *n_valid) {
+  if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
+  if (h->O < 1) return fail(h, FWH_ERR_STATE, "observers not set");
+  if (nt < 3 || nt > (int64_t)1 << 28) return fail(h, FWH_ERR_ARG, "nt must be >= 3");
+  fwh_status st = prepare_nt(h, nt);
+  if (st != FWH_OK) return st;
+  for (int64_t o = 0; o < h->O; ++o) {
+    if (t_start) t_start[o] = h->h_tstart[o];
+    if (n_valid) n_valid[o] = h->h_nvalid[o];
+  }
+  return FWH_OK;
+}
+
+fwh_status fwh_forward(fwh_handle h, const void *fields, int64_t nt, double *p_out,
+                       void *stream) {
+  if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
+  if (h->O < 1) return fail(h, FWH_ERR_STATE, "fwh_set_observers must come first");
+  if (!fields || !p_out) return fail(h, FWH_ERR_ARG, "fields or p_out is NULL");
+  if (nt < 3 || nt > (int64_t)1 << 28) return fail(h, FWH_ERR_ARG, "nt must be >= 3");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  fwh_status st = prepare_nt(h, nt);
+  if (st != FWH_OK) return st;
+  const size_t ts = tsize(h->precision);
+  const size_t fbytes = (size_t)nt * 5 * h->P * ts;
+  const size_t obytes = (size_t)h->O * nt * sizeof(double);
+  const bool din = is_device_ptr(fields), dout = is_device_ptr(p_out);
+  const void *df = fields;
+  double *dp = p_out;
+  if (!din) {
+    CK(h, ensure(h->stage_in, fbytes));
+    CK(h, cudaMemcpyAsync(h->stage_in.p, fields, fbytes, cudaMemcpyHostToDevice, s));
+    df = h->stage_in.p;
+  }
+  if (!dout) {
+    CK(h, ensure(h->stage_out, obytes));
+    dp = reinterpret_cast<double *>(h->stage_out.p);
+  }
+  st = h->precision == FWH_FP64
+           ? run_forward<double>(h, reinterpret_cast<const double *>(df), dp, s)
+           : run_forward<float>(h, reinterpret_cast<const float *>(df), dp, s);
+  if (st != FWH_OK) return st;
+  if (!dout) {
+    CK(h, cudaMemcpyAsync(p_out, dp, obytes, cudaMemcpyDeviceToHost, s));
+    return check_device_flag(h, s);
+  }
+  return FWH_OK;
+}
+
+fwh_status fwh_backward(fwh_handle h, const void *fields, int64_t nt, const double *grad_p,
+                        void *grad_fields, void *stream) {
+  if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
+  if (h->O < 1) return fail(h, FWH_ERR_STATE, "fwh_set_observers must come first");
+  if (!fields || !grad_p || !grad_fields)
+    return fail(h, FWH_ERR_ARG, "fields, grad_p or grad_fields is NULL");
+  if (nt < 3 || nt > (int64_t)1 << 28) return fail(h, FWH_ERR_ARG, "nt must be >= 3");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  fwh_status st = prepare_nt(h, nt);
+  if (st != FWH_OK) return st;
+  const size_t ts = tsize(h->precision);
+  const size_t fbytes = (size_t)nt * 5 * h->P * ts;
+  const size_t gbytes = (size_t)h->O * nt * sizeof(double);
+  const void *df = fields;
+  const double *dg = grad_p;
+  void *dgf = grad_fields;
+  const bool dout = is_device_ptr(grad_fields);
+  if (!is_device_ptr(fields)) {
+    CK(h, ensure(h->stage_in, fbytes));
+    CK(h, cudaMemcpyAsync(h->stage_in.p, fields, fbytes, cudaMemcpyHostToDevice, s));
+    df = h->stage_in.p;
+  }
+  if (!is_device_ptr(grad_p)) {
+    CK(h, ensure(h->stage_out, gbytes));
+    CK(h, cudaMemcpyAsync(h->stage_out.p, grad_p, gbytes, cudaMemcpyHostToDevice, s));
+    dg = reinterpret_cast<const double *>(h->stage_out.p);
+  }
+  if (!dout) {
+    CK(h, ensure(h->stage_grad, fbytes));
+    dgf = h->stage_grad.p;
+  }
+  CK(h, ensure(h->G, (size_t)h->O * h->ntp * ts));
+  if (h->precision == FWH_FP64) {
+    AdjArgs<double> aa{reinterpret_cast<const double *>(h->coef.p),
+                       reinterpret_cast<double *>(h->G.p), dg,
+                       reinterpret_cast<const int *>(h->nvalid.p),
+                       reinterpret_cast<double *>(h->X.p), (int)h->P, (int)h->O, h->ntp,
+                       (int)nt};
+    CK(h, launch_adjoint<double>(aa, s));
+    PrepAdjArgs<double> pa{reinterpret_cast<const double *>(df),
+                           h->identity ? nullptr : h->d_perm, h->d_n,
+                           reinterpret_cast<const double *>(h->X.p),
+                           reinterpret_cast<double *>(dgf), (int)h->P, (int)nt, h->ntp, 0,
+                           h->ca, h->sa, h->dt};
+    CK(h, launch_prep_adjoint<double>(pa, s));
+  } else {
+    AdjArgs<float> aa{reinterpret_cast<const float *>(h->coef.p),
+                      reinterpret_cast<float *>(h->G.p), dg,
+                      reinterpret_cast<const int *>(h->nvalid.p),
+                      reinterpret_cast<float *>(h->X.p), (int)h->P, (int)h->O, h->ntp, (int)nt};
+    CK(h, launch_adjoint<float>(aa, s));
+    PrepAdjArgs<float> pa{reinterpret_cast<const float *>(df),
+                          h->identity ? nullptr : h->d_perm, h->d_n,
+                          reinterpret_cast<const float *>(h->X.p),
+                          reinterpret_cast<float *>(dgf), (int)h->P, (int)nt, h->ntp, 0,
+                          h->ca, h->sa, h->dt};
+    CK(h, launch_prep_adjoint<float>(pa, s));
+  }
+  if (!dout) {
+    CK(h, cudaMemcpyAsync(grad_fields, dgf, fbytes, cudaMemcpyDeviceToHost, s));
+    return check_device_flag(h, s);
+  }
+  return FWH_OK;
+}
+
+fwh_status fwh_set_tile_config(fwh_handle h, int config) {
+  if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
+  if (config < -1 || config >= fwd_num_configs(h->precision == FWH_FP64))
+    return fail(h, FWH_ERR_ARG, "tile config out of range");
+  h->cfg = config;
+  drop_graphs(h);
+  return FWH_OK;
+}
+
+fwh_status fwh_autotune(fwh_handle h, int64_t nt, int *chosen, void *stream) {
+  if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
+  if (h->O < 1) return fail(h, FWH_ERR_STATE, "fwh_set_observers must come first");
+  if (nt < 3) return fail(h, FWH_ERR_ARG, "nt must be >= 3");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  fwh_status st = prepare_nt(h, nt);
+  if (st != FWH_OK) return st;
+  const size_t ts = tsize(h->precision);
+  Buf f, po;
+  CK(h, ensure(f, (size_t)nt * 5 * h->P * ts));
+  CK(h, ensure(po, (size_t)h->O * nt * sizeof(double)));
+  CK(h, cudaMemsetAsync(f.p, 0, f.bytes, s));
+  const bool was = h->timing;
+  const int old = h->cfg;
+  h->timing = true;
+  float best = 1e30f;
+  int besti = 0;
+  const int n = fwd_num_configs(h->precision == FWH_FP64);
+  for (int i = 0; i < n; ++i) {
+    h->cfg = i;
+    float tot = 0;
+    for (int rep = 0; rep < 3; ++rep) {
+      st = h->precision == FWH_FP64
+               ? run_forward<double>(h, reinterpret_cast<const double *>(f.p),
+                                     reinterpret_cast<double *>(po.p), s)
+               : run_forward<float>(h, reinterpret_cast<const float *>(f.p),
+                                    reinterpret_cast<double *>(po.p), s);
+      if (st != FWH_OK) break;
+      if (rep > 0) tot += h->last_ms[1];
+    }
+    if (st != FWH_OK) {
+      h->err.clear();
+      continue;
+    }
+    if (tot < best) {
+      best = tot;
+      besti = i;
+    }
+  }
+  release(f);
+  release(po);
+  h->timing = was;
+  h->cfg = besti;
+  (void)old;
+  if (chosen) *chosen = besti;
+  return FWH_OK;
+}
+
+fwh_status fwh_set_timing(fwh_handle h, int enable) {
+  if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
+  h->timing = enable != 0;
+  return FWH_OK;
+}
+
+fwh_status fwh_last_timings(fwh_handle h, float *ms3) {
+  if (!h || !ms3) return fail(h, FWH_ERR_ARG, "NULL argument");
+  for (int i = 0; i < 3; ++i) ms3[i] = h->last_ms[i];
+  return FWH_OK;
+}
+
+fwh_status fwh_get_sizes(fwh_handle h, int64_t *P, int64_t *O, int *precision) {
+  if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
+  if (P) *P = h->P;
+  if (O) *O = h->O;
+  if (precision) *precision = h->precision;
+  return FWH_OK;
+}
+
+void fwh_destroy(fwh_handle h) {
+  if (!h) return;
+  for (auto &kv : h->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  for (auto &kv : h->bplans) {
+    release(kv.second.args);
+    release(kv.second.prefix);
+    release(kv.second.counter);
+  }
+  for (double *p : {h->d_y, h->d_n, h->d_dS, h->d_x, h->d_Rmax, h->d_Rmin})
+    if (p) cudaFree(p);
+  if (h->d_perm) cudaFree(h->d_perm);
+  if (h->d_err) cudaFree(h->d_err);
+  for (Buf *b : {&h->coef, &h->X, &h->G, &h->nvalid, &h->sets, &h->stage_in, &h->stage_out,
+                 &h->stage_grad})
+    release(*b);
+  for (int i = 0; i < 4; ++i)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  for (int i = 0; i < 2; ++i)
+    if (h->bev[i]) cudaEventDestroy(h->bev[i]);
+  if (h->side) cudaStreamDestroy(h->side);
+  delete h;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched forward: several surfaces, one persistent work-queue launch.
+// Host-side planning and the upload of the per-surface argument table happen
+// once per argument set; the device work (output clears, integrand prep of
+// every surface, queue reset, persistent scatter) is captured in a CUDA graph
+// and replayed.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename T>
+fwh_status batch_build(int n, const fwh_handle *hs, const void *const *fields,
+                       double *const *p_out, fwh_handle h0, BatchPlan &bp) {
+  const bool fp64 = sizeof(T) == 8;
+  const int cfg = h0->cfg >= 0 ? h0->cfg : default_cfg(h0);
+  const FwdConfig c = fwd_config(fp64, cfg);
+  std::vector<FwdArgs<T>> args(n);
+  std::vector<int> prefix(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    fwh_handle h = hs[i];
+    fwh_status st = plan(h, c);
+    if (st != FWH_OK) return fail(h0, st, h->err);
+    FwdArgs<T> &fa = args[i];
+    fa.X = reinterpret_cast<const T *>(h->X.p);
+    fa.coef = reinterpret_cast<const T *>(h->coef.p);
+    fa.p_out = p_out[i];
+    fa.n_valid = reinterpret_cast<const int *>(h->nvalid.p);
+    fa.set_begin = reinterpret_cast<const int *>(h->sets.p);
+    fa.err = h0->d_err;
+    fa.nsets = (int)h->set_begin.size() - 1;
+    fa.O = (int)h->O;
+    fa.ntp = h->ntp;
+    fa.nt = (int)h->nt;
+    obs_tiling(h, c, &fa.obs_per_cta, &fa.n_obs_groups);
+    fa.seg_len = c.seg_chunks * 32 * c.tk;
+    fa.n_segs = (h->ntp + fa.seg_len - 1) / fa.seg_len;
+    fa.win = c.win;
+    prefix[i + 1] = prefix[i] + fa.nsets * fa.n_obs_groups * fa.n_segs;
+  }
+  (void)fields;
+  bp.total = prefix[n];
+  bp.cfg = cfg;
+  CK(h0, ensure(bp.args, n * sizeof(FwdArgs<T>)));
+  CK(h0, ensure(bp.prefix, (n + 1) * sizeof(int)));
+  CK(h0, ensure(bp.counter, sizeof(int)));
+  CK(h0, cudaMemcpy(bp.args.p, args.data(), n * sizeof(FwdArgs<T>), cudaMemcpyHostToDevice));
+  CK(h0, cudaMemcpy(bp.prefix.p, prefix.data(), (n + 1) * sizeof(int),
+                    cudaMemcpyHostToDevice));
+  int dev = 0, sms = 0;
+  CK(h0, cudaGetDevice(&dev));
+  CK(h0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  bp.ctas = std::max(1, std::min(bp.total, sms * 2));
+  return FWH_OK;
+}
+
+template <typename T>
+fwh_status batch_enqueue(int n, const fwh_handle *hs, const void *const *fields,
+                         double *const *p_out, fwh_handle h0, const BatchPlan &bp,
+                         cudaStream_t s) {
+  for (int i = 0; i < n; ++i) {
+    fwh_handle h = hs[i];
+    CK(h0, cudaMemsetAsync(p_out[i], 0, (size_t)h->O * h->nt * sizeof(double), s));
+    PrepArgs<T> pa{};
+    pa.fields = reinterpret_cast<const T *>(fields[i]);
+    pa.perm = h->identity ? nullptr : h->d_perm;
+    pa.n = h->d_n;
+    pa.X = reinterpret_cast<T *>(h->X.p);
+    pa.P = (int)h->P;
+    pa.nt = (int)h->nt;
+    pa.ntp = h->ntp;
+    pa.ca = h->ca;
+    pa.sa = h->sa;
+    pa.dt = h->dt;
+    CK(h0, launch_prep<T>(pa, s));
+  }
+  CK(h0, cudaMemsetAsync(bp.counter.p, 0, sizeof(int), s));
+  CK(h0, launch_forward_batch<T>(reinterpret_cast<const FwdArgs<T> *>(bp.args.p),
+                                 reinterpret_cast<const int *>(bp.prefix.p), n, bp.total,
+                                 reinterpret_cast<int *>(bp.counter.p), bp.cfg, bp.ctas, s));
+  return FWH_OK;
+}
+
+}  // namespace
+
+extern "C" fwh_status fwh_batch_forward(int n, const fwh_handle *hs, const void *const *fields,
+                                        const int64_t *nt, double *const *p_out,
+                                        void *stream) {
+  if (n < 1 || !hs || !fields || !nt || !p_out)
+    return fail(nullptr, FWH_ERR_ARG, "invalid batch arguments");
+  fwh_handle h0 = hs[0];
+  if (!h0) return fail(nullptr, FWH_ERR_ARG, "NULL handle in batch");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int i = 0; i < n; ++i) {
+    fwh_handle h = hs[i];
+    if (!h || !fields[i] || !p_out[i]) return fail(h0, FWH_ERR_ARG, "NULL entry in batch");
+    if (h->precision != h0->precision) return fail(h0, FWH_ERR_ARG, "mixed precisions in batch");
+    if (h->O < 1) return fail(h0, FWH_ERR_STATE, "a handle has no observers");
+    if (nt[i] < 3) return fail(h0, FWH_ERR_ARG, "nt must be >= 3");
+    if (!is_device_ptr(fields[i]) || !is_device_ptr(p_out[i]))
+      return fail(h0, FWH_ERR_ARG, "batched forward takes device buffers");
+    fwh_status st = prepare_nt(h, nt[i]);
+    if (st != FWH_OK) return fail(h0, st, h->err);
+  }
+  std::vector<uintptr_t> key;
+  for (int i = 0; i < n; ++i) {
+    key.push_back((uintptr_t)hs[i]);
+    key.push_back((uintptr_t)fields[i]);
+    key.push_back((uintptr_t)p_out[i]);
+    key.push_back((uintptr_t)nt[i]);
+    key.push_back((uintptr_t)hs[i]->X.p);
+    key.push_back((uintptr_t)hs[i]->coef.p);
+    key.push_back((uintptr_t)hs[i]->O);
+    key.push_back((uintptr_t)hs[i]->nvalid.p);
+    key.push_back((uintptr_t)hs[i]->sets.p);
+  }
+  key.push_back((uintptr_t)(h0->cfg + 1));
+  if (!h0->side) {
+    CK(h0, cudaStreamCreateWithFlags(&h0->side, cudaStreamNonBlocking));
+    CK(h0, cudaEventCreateWithFlags(&h0->bev[0], cudaEventDisableTiming));
+    CK(h0, cudaEventCreateWithFlags(&h0->bev[1], cudaEventDisableTiming));
+  }
+  auto it = h0->graphs.find(key);
+  if (it == h0->graphs.end()) {
+    BatchPlan &bp = h0->bplans[key];
+    fwh_status st = h0->precision == FWH_FP64 ? batch_build<double>(n, hs, fields, p_out, h0, bp)
+                                              : batch_build<float>(n, hs, fields, p_out, h0, bp);
+    if (st != FWH_OK) return st;
+    // capture on the side stream (the caller's may be the legacy stream)
+    cudaGraph_t g = nullptr;
+    CK(h0, cudaStreamBeginCapture(h0->side, cudaStreamCaptureModeThreadLocal));
+    st = h0->precision == FWH_FP64
+             ? batch_enqueue<double>(n, hs, fields, p_out, h0, bp, h0->side)
+             : batch_enqueue<float>(n, hs, fields, p_out, h0, bp, h0->side);
+    cudaError_t e = cudaStreamEndCapture(h0->side, &g);
+    if (st != FWH_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(h0, e, "cudaStreamEndCapture");
+    Graph gr;
+    e = cudaGraphInstantiate(&gr.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h0, e, "cudaGraphInstantiate");
+    gr.key = key;
+    it = h0->graphs.emplace(key, gr).first;
+  }
+  CK(h0, cudaEventRecord(h0->bev[0], s));
+  CK(h0, cudaStreamWaitEvent(h0->side, h0->bev[0], 0));
+  CK(h0, cudaGraphLaunch(it->second.exec, h0->side));
+  CK(h0, cudaEventRecord(h0->bev[1], h0->side));
+  CK(h0, cudaStreamWaitEvent(s, h0->bev[1], 0));
+  return FWH_OK;
+}
+
+extern "C" fwh_status fwh_check(fwh_handle h, void *stream) {
+  if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
+  return check_device_flag(h, reinterpret_cast<cudaStream_t>(stream));
+}

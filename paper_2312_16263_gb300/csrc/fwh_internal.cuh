@@ -1,0 +1,134 @@
+// Internal declarations of the GB300 FW-H library (not part of the C ABI).
+//
+// Data layout in HBM (P = panels in the library's spatial order, O =
+// observers, ntp = nt rounded up to the forward chunk, T = float or double):
+//   fields   [nt][5][P]      caller's pulsations (original panel order)
+//   X        [P][ntp][16] T  per panel, per source sample: the eight
+//                            observer-independent series
+//                              0 Qn_dot 1 Qn 2..4 L_dot 5..7 L
+//                            then their natural-spline moments (8..15);
+//                            rows >= nt are zero
+//   coef     [P][O][16] T    per (panel, observer): 8 integrand coefficients
+//                            (same order as X), then the interpolation
+//                            weights a, b, cc, dd and the integer shift i0
+//                            (bit pattern in slot 12 for float, value for
+//                            double), slots 13..15 unused
+//   p_out    [O][nt] double  caller's output
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fwh {
+
+constexpr int kRec = 16;          // values per X row and per coef record
+constexpr int kWarp = 32;
+
+// Halo (samples) of the windowed natural-spline solves: the influence of a
+// window edge decays as (2 - sqrt 3)^k, below 1e-18 for k = 32 and below
+// 1e-9 (under FP32 rounding) for k = 16.
+template <typename T> struct Prec;
+template <> struct Prec<float> { static constexpr int halo = 16; };
+template <> struct Prec<double> { static constexpr int halo = 32; };
+
+constexpr int kPivTab = 64;       // 1/pivot of the tridiag(1,4,1) elimination
+
+// Device error flags (bitmask written by kernels, read by the host).
+enum : int {
+  kErrWindow = 1,      // a panel set's arrival spread exceeded the window
+  kErrTimeout = 2,     // a bounded wait gave up
+  kErrQueue = 4,       // persistent queue inconsistency
+};
+
+struct GeomArgs {
+  const double *y;      // [P][3] sorted centroids
+  const double *n;      // [P][3] sorted normals
+  const double *dS;     // [P]
+  const double *x;      // [O][3]
+  int P, O;
+  double mach, ca, sa, dt;
+  double *Rmax, *Rmin;  // [O]
+};
+
+template <typename T>
+struct PrepArgs {
+  const T *fields;      // [nt][5][P] original order
+  const int *perm;      // [P] sorted position -> original panel index
+  const double *n;      // [P][3] sorted normals
+  T *X;                 // [P][ntp][16]
+  int P, nt, ntp, chunk;
+  double ca, sa, dt;
+};
+
+template <typename T>
+struct FwdArgs {
+  const T *X;           // [P][ntp][16]
+  const T *coef;        // [P][O][16]
+  double *p_out;        // [O][nt]
+  const int *n_valid;   // [O]
+  const int *set_begin; // [nsets + 1] panel-set boundaries (sorted order)
+  int *err;
+  int nsets, O, ntp, nt;
+  int obs_per_cta, n_obs_groups;
+  int seg_len, n_segs;
+  int win;              // window slots per observer
+};
+
+template <typename T>
+struct AdjArgs {
+  const T *coef;        // [P][O][16]
+  T *Gt;                // [O][ntp] workspace: grad_p in T, zero outside [0, N_o)
+  const double *grad_p; // [O][nt]
+  const int *n_valid;   // [O]
+  T *Xbar;              // [P][ntp][16] gradient w.r.t. X
+  int P, O, ntp, nt;
+};
+
+template <typename T>
+struct PrepAdjArgs {
+  const T *fields;      // [nt][5][P] original order
+  const int *perm;
+  const double *n;      // [P][3] sorted normals
+  const T *Xbar;        // [P][ntp][16]
+  T *grad_fields;       // [nt][5][P] original order
+  int P, nt, ntp, chunk;
+  double ca, sa, dt;
+};
+
+// ---- launchers (defined in the .cu files) --------------------------------
+cudaError_t launch_window(const GeomArgs &a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_coef(const GeomArgs &a, T *coef, cudaStream_t s);
+cudaError_t upload_pivots(cudaStream_t s);
+template <typename T>
+cudaError_t launch_prep(const PrepArgs<T> &a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prep_adjoint(const PrepAdjArgs<T> &a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adjoint(const AdjArgs<T> &a, cudaStream_t s);
+
+// Forward tile configurations (index into a table in fwh_forward.cu).
+struct FwdConfig {
+  int tk;             // source samples per lane per chunk (chunk = 32 tk)
+  int warps;          // warps per CTA
+  int obs_per_warp;   // max observers per warp
+  int win;            // window slots per observer
+  int seg_chunks;     // chunks per time segment
+};
+int fwd_num_configs(bool fp64);
+FwdConfig fwd_config(bool fp64, int idx);
+template <typename T>
+cudaError_t launch_forward(const FwdArgs<T> &a, int cfg_idx, cudaStream_t s);
+
+// Batched persistent forward.
+template <typename T>
+struct BatchItemDesc {
+  FwdArgs<T> args;          // per-surface arguments
+  int items;                // work items of this surface
+};
+template <typename T>
+cudaError_t launch_forward_batch(const FwdArgs<T> *d_args, const int *d_item_prefix,
+                                 int n_surf, int total_items, int *d_counter,
+                                 int cfg_idx, int n_ctas, cudaStream_t s);
+
+}  // namespace fwh

@@ -1,0 +1,308 @@
+// Observer-independent source-time series of the FW-H integrand ("compute
+// Noise", Sec. III B), per panel and source sample:
+//   Qn  = rho' (U.n) + (1 + rho') (u'.n)                  (Eq. Qn_New_nd)
+//   L_c = p' n_c + (1 + rho') u'_c (U.n + u'.n)           (Eq. Li_New_nd)
+// in pulsation-expanded form (no cancellation of O(1) terms in FP32), their
+// second-order source-time derivatives (central inside, one-sided 3-point at
+// the first and last frame), and the natural-cubic-spline second derivatives
+// ("moments") of all eight series, used by the spline interpolation onto the
+// observer grid ("interp pressure signal").  The spline of the per-panel
+// signal sum_s c_s F_s has moments sum_s c_s m(F_s) by linearity, so the
+// moments are computed once per panel instead of once per (panel, observer).
+//
+// The moments solve, on a window of the chunk plus a halo of H samples on
+// each side (clipped to the record), the tridiagonal system
+//   m_{j-1} + 4 m_j + m_{j+1} = 6 (F_{j+1} - 2 F_j + F_{j-1}) / dt^2
+// with m = 0 at the window ends: at the record ends this is the natural end
+// condition itself; at an artificial end the error decays as (2 - sqrt 3)^H
+// into the chunk, below the arithmetic's rounding for the chosen H.
+//
+// Thread mapping: a CTA is 16 panels x 8 series, one thread per
+// (panel, series), sequential over the window in source time; the forward
+// elimination's values for the chunk and right halo wait in shared memory
+// for the back substitution (interleaved by thread: conflict-free).
+#include "fwh_internal.cuh"
+
+namespace fwh {
+
+__constant__ float c_inv_piv_f[kPivTab];
+__constant__ double c_inv_piv_d[kPivTab];
+
+cudaError_t upload_pivots(cudaStream_t s) {
+  // 1/pivot of Gaussian elimination of tridiag(1, 4, 1) started at row 1:
+  // piv_1 = 4, piv_j = 4 - 1/piv_{j-1}  (converges to 2 + sqrt 3).
+  double invd[kPivTab];
+  float invf[kPivTab];
+  double piv = 4.0;
+  invd[0] = 0.0;
+  invf[0] = 0.0f;
+  for (int j = 1; j < kPivTab; ++j) {
+    if (j > 1) piv = 4.0 - invd[j - 1];
+    invd[j] = 1.0 / piv;
+    invf[j] = (float)invd[j];
+  }
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_inv_piv_d, invd, sizeof(invd), 0,
+                                          cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbolAsync(c_inv_piv_f, invf, sizeof(invf), 0, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
+namespace {
+
+template <typename T> __device__ __forceinline__ T inv_piv(int j);
+template <> __device__ __forceinline__ float inv_piv<float>(int j) {
+  return c_inv_piv_f[j < kPivTab ? j : kPivTab - 1];
+}
+template <> __device__ __forceinline__ double inv_piv<double>(int j) {
+  return c_inv_piv_d[j < kPivTab ? j : kPivTab - 1];
+}
+
+constexpr int kPanelsPerCta = 16;
+constexpr int kThreads = kPanelsPerCta * 8;
+
+template <typename T> struct PrepChunk;
+template <> struct PrepChunk<float> { static constexpr int v = 128; };
+template <> struct PrepChunk<double> { static constexpr int v = 64; };
+
+// Integrand `which` (0: Qn, 1..3: L_c) of panel po at sample i.
+template <typename T>
+struct Integrand {
+  const T *f;
+  int P, po, which;
+  T n0, n1, n2, nc, Un;
+  __device__ __forceinline__ T operator()(int i) const {
+    const T *b = f + (size_t)i * 5 * P + po;
+    const T rho = b[0];
+    const T u0 = b[(size_t)P], u1 = b[2 * (size_t)P], u2 = b[3 * (size_t)P];
+    const T un = u0 * n0 + u1 * n1 + u2 * n2;
+    if (which == 0) return rho * Un + (T(1) + rho) * un;
+    const T pp = b[4 * (size_t)P];
+    const T uc = which == 1 ? u0 : (which == 2 ? u1 : u2);
+    return pp * nc + (T(1) + rho) * uc * (Un + un);
+  }
+};
+
+// Series value F_s(i): the integrand or its second-order FD derivative.
+template <typename T>
+__device__ __forceinline__ T series_at(const Integrand<T> &g, bool deriv, int i, int nt,
+                                       T inv2h) {
+  if (!deriv) return g(i);
+  if (i == 0) return (T(-3) * g(0) + T(4) * g(1) - g(2)) * inv2h;
+  if (i == nt - 1) return (T(3) * g(nt - 1) - T(4) * g(nt - 2) + g(nt - 3)) * inv2h;
+  return (g(i + 1) - g(i - 1)) * inv2h;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_prep(PrepArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *zbuf = reinterpret_cast<T *>(smem_raw);
+  const int tid = threadIdx.x;
+  const int s = tid & 7;
+  const int p = blockIdx.x * kPanelsPerCta + (tid >> 3);
+  if (p >= a.P) return;
+  const int c0 = blockIdx.y * a.chunk;
+  const int c1 = min(c0 + a.chunk, a.ntp);
+  const int nt = a.nt;
+  T *Xp = a.X + (size_t)p * a.ntp * kRec;
+
+  // zero rows beyond the record
+  for (int i = max(c0, nt); i < c1; ++i) {
+    Xp[(size_t)i * kRec + s] = T(0);
+    Xp[(size_t)i * kRec + 8 + s] = T(0);
+  }
+  if (c0 >= nt) return;
+  const int ce = min(c1, nt);
+
+  Integrand<T> g;
+  g.f = a.fields;
+  g.P = a.P;
+  g.po = a.perm ? a.perm[p] : p;
+  g.n0 = (T)a.n[3 * p];
+  g.n1 = (T)a.n[3 * p + 1];
+  g.n2 = (T)a.n[3 * p + 2];
+  g.Un = (T)(a.ca * a.n[3 * p] + a.sa * a.n[3 * p + 1]);
+  const bool deriv = (s == 0) || (s >= 2 && s <= 4);
+  g.which = (s <= 1) ? 0 : 1 + (s - 2) % 3;
+  g.nc = g.which == 1 ? g.n0 : (g.which == 2 ? g.n1 : g.n2);
+  const T inv2h = (T)(0.5 / a.dt);
+  const T s6 = (T)(6.0 / (a.dt * a.dt));
+
+  constexpr int H = Prec<T>::halo;
+  const int wa = max(0, c0 - H), wb = min(nt, ce + H);
+  const int L = wb - wa;
+
+  T Fprev = T(0), Fcur = series_at(g, deriv, wa, nt, inv2h), z = T(0);
+  for (int i = wa; i < wb; ++i) {
+    const int j = i - wa;
+    const T Fnext = (i + 1 < wb) ? series_at(g, deriv, i + 1, nt, inv2h) : T(0);
+    if (i >= c0 && i < ce) Xp[(size_t)i * kRec + s] = Fcur;
+    if (j >= 1 && j <= L - 2) {
+      const T r = s6 * (Fnext - T(2) * Fcur + Fprev);
+      z = (r - z) * inv_piv<T>(j);
+      if (i >= c0) zbuf[(size_t)(i - c0) * kThreads + tid] = z;
+    }
+    Fprev = Fcur;
+    Fcur = Fnext;
+  }
+  // back substitution over the chunk (+ right halo); m = 0 at window ends
+  T mnext = T(0);
+  if (wb - 1 >= c0 && wb - 1 < ce) Xp[(size_t)(wb - 1) * kRec + 8 + s] = T(0);
+  for (int i = wb - 2; i >= c0 && i >= wa + 1; --i) {
+    const int j = i - wa;
+    const T m = zbuf[(size_t)(i - c0) * kThreads + tid] - mnext * inv_piv<T>(j);
+    if (i < ce) Xp[(size_t)i * kRec + 8 + s] = m;
+    mnext = m;
+  }
+  if (wa == c0) Xp[(size_t)c0 * kRec + 8 + s] = T(0);  // record start: m_0 = 0
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of k_prep followed by the Jacobian of the integrands.
+// Xbar[p][i][s] = dLoss/dF_s(i), Xbar[p][i][8+s] = dLoss/dm_s(i).  For each
+// series: G_s = Xbar_s + (6/dt^2) D2^T T^{-1} mbar (transpose of the moment
+// solve; the interior matrix is symmetric), then the integrand gradient is
+// G_s (value series) or D1^T G_s (derivative series), summed per integrand
+// over the 8 threads of a panel, and mapped to the five field gradients.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_prep_adj(PrepAdjArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *zb = reinterpret_cast<T *>(smem_raw);
+  const int tid = threadIdx.x;
+  const int s = tid & 7;
+  const int p = blockIdx.x * kPanelsPerCta + (tid >> 3);
+  const bool live = p < a.P;
+  const int c0 = blockIdx.y * a.chunk;
+  const int nt = a.nt;
+  const int ce = min(c0 + a.chunk, nt);
+  if (c0 >= nt) return;  // uniform across the CTA
+  const int pp = live ? p : a.P - 1;
+  const T *Xb = a.Xbar + (size_t)pp * a.ntp * kRec;
+  const bool deriv = (s == 0) || (s >= 2 && s <= 4);
+  const T inv2h = (T)(0.5 / a.dt);
+  const T s6 = (T)(6.0 / (a.dt * a.dt));
+  constexpr int H = Prec<T>::halo;
+  // z = T^{-1} mbar is needed on [e0, e1) = [c0 - 3, ce + 3) for G on
+  // [c0 - 2, ce + 2) and D1^T on [c0, ce).
+  const int e0 = max(0, c0 - 3), e1 = min(nt, ce + 3);
+  const int wa = max(0, e0 - H), wb = min(nt, e1 + H);
+  const int L = wb - wa;
+  // forward elimination; z kept from e0 to the right end of the window
+  T z = T(0);
+  for (int i = wa + 1; i <= wb - 2; ++i) {
+    const int j = i - wa;
+    const T mb = Xb[(size_t)i * kRec + 8 + s];
+    z = (mb - z) * inv_piv<T>(j);
+    if (i >= e0) zb[(size_t)(i - e0) * kThreads + tid] = z;
+  }
+  // back substitution (window ends and record ends hold z = 0)
+  T znext = T(0);
+  for (int i = wb - 1; i >= e0; --i) {
+    const int j = i - wa;
+    T zz;
+    if (j == 0 || j == L - 1) {
+      zz = T(0);
+    } else {
+      zz = zb[(size_t)(i - e0) * kThreads + tid] - znext * inv_piv<T>(j);
+    }
+    zb[(size_t)(i - e0) * kThreads + tid] = zz;
+    znext = zz;
+  }
+  __syncwarp();
+  auto zat = [&](int i) -> T {
+    if (i < e0 || i >= e1 || i <= 0 || i >= nt - 1) return T(0);
+    return zb[(size_t)(i - e0) * kThreads + tid];
+  };
+  auto Gat = [&](int i) -> T {
+    return Xb[(size_t)i * kRec + s] + s6 * (zat(i - 1) - T(2) * zat(i) + zat(i + 1));
+  };
+  // field gradients for this chunk
+  const int po = live ? (a.perm ? a.perm[p] : p) : 0;
+  const T n0 = (T)a.n[3 * pp], n1 = (T)a.n[3 * pp + 1], n2 = (T)a.n[3 * pp + 2];
+  const T Un = (T)(a.ca * a.n[3 * pp] + a.sa * a.n[3 * pp + 1]);
+  for (int i = c0; i < ce; ++i) {
+    T c;
+    if (!deriv) {
+      c = Gat(i);
+    } else {
+      // transpose of the FD derivative at integrand sample i
+      c = T(0);
+      if (i - 1 >= 1 && i - 1 <= nt - 2) c += Gat(i - 1) * inv2h;
+      if (i + 1 >= 1 && i + 1 <= nt - 2) c -= Gat(i + 1) * inv2h;
+      if (i <= 2) {
+        const T w0 = (i == 0) ? T(-3) : (i == 1 ? T(4) : T(-1));
+        c += w0 * inv2h * Gat(0);
+      }
+      if (i >= nt - 3) {
+        const T w1 = (i == nt - 1) ? T(3) : (i == nt - 2 ? T(-4) : T(1));
+        c += w1 * inv2h * Gat(nt - 1);
+      }
+    }
+    // integrand gradients: Qn from series 0,1; L_c from series 2+c and 5+c
+    const int base = (tid & 31) & ~7;
+    T v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __shfl_sync(0xffffffffu, c, base + k);
+    const T qb = v[0] + v[1];
+    const T lb0 = v[2] + v[5], lb1 = v[3] + v[6], lb2 = v[4] + v[7];
+    if (live && s < 5) {
+      const T *fb = a.fields + (size_t)i * 5 * a.P + po;
+      const T rho = fb[0], u0 = fb[(size_t)a.P], u1 = fb[2 * (size_t)a.P],
+              u2 = fb[3 * (size_t)a.P];
+      const T un = u0 * n0 + u1 * n1 + u2 * n2;
+      const T utn = Un + un;  // total u . n
+      const T r1 = T(1) + rho;
+      const T lu = lb0 * u0 + lb1 * u1 + lb2 * u2;
+      T out;
+      if (s == 0) {
+        // dQn/drho' = U.n + u'.n ; dL_c/drho' = u'_c (U.n + u'.n)
+        out = qb * utn + lu * utn;
+      } else if (s <= 3) {
+        // dQn/du'_k = (1 + rho') n_k ; dL_c/du'_k = (1 + rho')(delta_ck u.n + u'_c n_k)
+        const T nk = s == 1 ? n0 : (s == 2 ? n1 : n2);
+        const T lk = s == 1 ? lb0 : (s == 2 ? lb1 : lb2);
+        out = qb * r1 * nk + lk * r1 * utn + r1 * lu * nk;
+      } else {
+        out = lb0 * n0 + lb1 * n1 + lb2 * n2;  // dL_c/dp' = n_c
+      }
+      a.grad_fields[((size_t)i * 5 + s) * a.P + po] = out;
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_prep(const PrepArgs<T> &a0, cudaStream_t s) {
+  PrepArgs<T> a = a0;
+  a.chunk = PrepChunk<T>::v;
+  const size_t smem = (size_t)(a.chunk + Prec<T>::halo) * kThreads * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(k_prep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.P + kPanelsPerCta - 1) / kPanelsPerCta, (a.ntp + a.chunk - 1) / a.chunk);
+  k_prep<T><<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prep_adjoint(const PrepAdjArgs<T> &a0, cudaStream_t s) {
+  PrepAdjArgs<T> a = a0;
+  a.chunk = PrepChunk<T>::v;
+  const size_t smem = (size_t)(a.chunk + 6 + Prec<T>::halo) * kThreads * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(k_prep_adj<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.P + kPanelsPerCta - 1) / kPanelsPerCta, (a.nt + a.chunk - 1) / a.chunk);
+  k_prep_adj<T><<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_prep<float>(const PrepArgs<float> &, cudaStream_t);
+template cudaError_t launch_prep<double>(const PrepArgs<double> &, cudaStream_t);
+template cudaError_t launch_prep_adjoint<float>(const PrepAdjArgs<float> &, cudaStream_t);
+template cudaError_t launch_prep_adjoint<double>(const PrepAdjArgs<double> &, cudaStream_t);
+
+}  // namespace fwh

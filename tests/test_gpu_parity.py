@@ -1,0 +1,195 @@
+"""CUDA path vs the FP64 CPU oracle, element by element (needs a GPU).
+
+Tolerances (spec contract): rel-L2 per observer signal <= 1e-10 for the
+FP64 path and <= 1e-4 for the mixed path, compared on the common prefix of
+the two observer windows (N_o comes from a floor() of FP64 values that may
+round differently).  Cases span several tiles with ragged tails: panel
+counts that are not multiples of the 16-panel prep tile or the 64-panel set,
+record lengths that are not multiples of the 128-sample chunk, one observer,
+unstructured (Morton-ordered) geometry, high Mach and negative AoA.
+"""
+import numpy as np
+import pytest
+import torch
+
+from fwh_inputs import FlowCase, observers_circle, uv_sphere, workload
+from fwh_inputs.analytic import surface_fields
+from oracle import Oracle
+
+pytestmark = pytest.mark.gpu
+DEG = np.pi / 180
+TOL = {"fp64": 1e-10, "mixed": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from __graft_entry__ import build
+    build()
+    return torch.device("cuda:0")
+
+
+def _fwh(surf, mach, aoa, dt, prec, obs):
+    from paper_2312_16263_gb300 import FWH
+    return FWH(surf.centroids, surf.normals, surf.areas, mach, aoa, dt, prec, observers=obs)
+
+
+def _compare(p_gpu, nv_gpu, p_ref, nv_ref, tol, label=""):
+    worst = 0.0
+    for o in range(p_ref.shape[0]):
+        n = int(min(nv_gpu[o], nv_ref[o]))
+        assert abs(int(nv_gpu[o]) - int(nv_ref[o])) <= 1, (label, o, nv_gpu[o], nv_ref[o])
+        if n == 0:
+            continue
+        ref = p_ref[o, :n]
+        den = np.linalg.norm(ref)
+        err = np.linalg.norm(p_gpu[o, :n] - ref) / den if den > 0 else np.abs(p_gpu[o, :n]).max()
+        worst = max(worst, err)
+        # bins beyond the window are exactly zero
+        assert np.all(p_gpu[o, nv_gpu[o]:] == 0.0), (label, o)
+    assert worst <= tol, (label, worst)
+    return worst
+
+
+def _run_case(dev, surf, mach, aoa, dt, fields64, obs, prec):
+    s = _fwh(surf, mach, aoa, dt, prec, obs)
+    f = torch.as_tensor(fields64).to(device=dev, dtype=s.dtype).contiguous()
+    p = s.forward(f).cpu().numpy()
+    ts, nv = s.window(fields64.shape[0])
+    s.check()
+    orc = Oracle(surf.centroids, surf.normals, surf.areas, mach, aoa, dt)
+    # the oracle sees exactly the values the GPU saw (float32 inputs upcast)
+    p_ref, ts_ref, nv_ref = orc.forward(f.double().cpu().numpy(), obs)
+    np.testing.assert_allclose(ts, ts_ref, rtol=1e-13, atol=0)
+    return p, nv, p_ref, nv_ref, s
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_workload1_parity(dev, prec):
+    w = workload(1)
+    p, nv, p_ref, nv_ref, _ = _run_case(dev, w.surface, w.mach, w.aoa, w.dt,
+                                        w.fields().numpy(), w.observers, prec)
+    _compare(p, nv, p_ref, nv_ref, TOL[prec], "workload1")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["ragged", "min_nt", "one_obs", "unstructured", "high_mach",
+                                  "many_obs"])
+def test_edge_cases(dev, prec, case):
+    rng = np.random.default_rng(abs(hash(case)) % 2**32)
+    mach, aoa, dt = 0.35, -12 * DEG, 0.03
+    surf = uv_sphere(1.0, 7, 11)          # 77 panels: ragged vs 16/64
+    nt = 301                              # ragged vs the 128-sample chunk
+    obs = observers_circle(25.0, 5) + rng.normal(size=(5, 3))
+    if case == "min_nt":
+        nt = 3
+        obs = observers_circle(3.0, 3)
+    elif case == "one_obs":
+        obs = np.array([[0.0, -30.0, 2.0]])
+    elif case == "unstructured":
+        pts = rng.normal(size=(600, 3))
+        pts /= np.linalg.norm(pts, axis=1, keepdims=True)
+        from fwh_inputs.geometry import Surface
+        surf = Surface(pts * 1.3, pts.copy(), rng.uniform(0.5, 1.5, 600) * 4 * np.pi * 1.69 / 600)
+        nt = 700
+    elif case == "high_mach":
+        mach, aoa, dt = 0.9, 30 * DEG, 0.02
+        nt = 513
+    elif case == "many_obs":
+        obs = observers_circle(40.0, 150)
+        nt = 260
+    flow = FlowCase(mach, aoa)
+    f = surface_fields("monopole", surf.centroids, flow, 0.01, 2 * np.pi, dt, nt)
+    f += rng.normal(size=f.shape) * 1e-4      # break symmetry, exercise all terms
+    p, nv, p_ref, nv_ref, _ = _run_case(dev, surf, mach, aoa, dt, f, obs, prec)
+    _compare(p, nv, p_ref, nv_ref, TOL[prec], case)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_workload2_full_size_sampled(dev, prec):
+    """Full workload 2 (32768 panels x 2048 steps x 72 observers) in the
+    bench's launch configuration; the oracle checks 4 sampled observers."""
+    w = workload(2)
+    from paper_2312_16263_gb300 import FWH
+    s = FWH.from_workload(w, prec)
+    f = w.fields(device=dev, dtype="float64" if prec == "fp64" else "float32")
+    p = s.forward(f).cpu().numpy()
+    s.check()
+    _, nv = s.window(w.nt)
+    pick = np.array([0, 18, 41, 63])
+    orc = Oracle.from_workload(w)
+    p_ref, _, nv_ref = orc.forward(f.double().cpu().numpy(), w.observers[pick])
+    _compare(p[pick], nv[pick], p_ref, nv_ref, TOL[prec], "workload2")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_host_pointer_path_matches_device(dev, prec):
+    w = workload(1, scale=0.5)
+    from paper_2312_16263_gb300 import FWH
+    s = FWH.from_workload(w, prec)
+    f = w.fields(dtype="float64" if prec == "fp64" else "float32")
+    p_host = s.forward(f.contiguous())          # host in, host out (staged)
+    p_dev = s.forward(f.to(dev)).cpu()
+    assert p_host.device.type == "cpu"
+    assert torch.allclose(p_host, p_dev, rtol=0, atol=1e-14 * p_dev.abs().max().item())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_backward_matches_oracle_adjoint(dev, prec):
+    rng = np.random.default_rng(5)
+    surf = uv_sphere(1.0, 9, 13)
+    mach, aoa, dt, nt = 0.45, 8 * DEG, 0.04, 333
+    obs = observers_circle(20.0, 6) + rng.normal(size=(6, 3))
+    f = surface_fields("dipole", surf.centroids, FlowCase(mach, aoa), 0.01, 2 * np.pi, dt, nt)
+    f += rng.normal(size=f.shape) * 1e-3
+    s = _fwh(surf, mach, aoa, dt, prec, obs)
+    ft = torch.as_tensor(f).to(device=dev, dtype=s.dtype).contiguous()
+    g_out = torch.as_tensor(rng.normal(size=(obs.shape[0], nt)), device=dev)
+    g = s.backward(ft, g_out).double().cpu().numpy()
+    s.check()
+    orc = Oracle(surf.centroids, surf.normals, surf.areas, mach, aoa, dt)
+    g_ref = orc.backward(ft.double().cpu().numpy(), obs, g_out.cpu().numpy())
+    err = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    assert err <= (1e-10 if prec == "fp64" else 1e-4), err
+
+
+def test_batch_forward_matches_single(dev):
+    from paper_2312_16263_gb300 import FWH, batch_forward
+    rng = np.random.default_rng(11)
+    surfs, fields, singles = [], [], []
+    for i, (npol, naz, nt, no) in enumerate([(8, 16, 200, 5), (13, 7, 131, 9), (20, 40, 390, 3)]):
+        sf = uv_sphere(1.0 + 0.3 * i, npol, naz, center=(i, 0, 0))
+        obs = observers_circle(30.0, no) + rng.normal(size=(no, 3))
+        s = FWH(sf.centroids, sf.normals, sf.areas, 0.3 + 0.1 * i, 0.1 * i, 0.02, "mixed",
+                observers=obs)
+        f = torch.as_tensor(rng.normal(size=(nt, 5, sf.n_panels)) * 1e-3,
+                            dtype=torch.float32, device=dev)
+        surfs.append(s)
+        fields.append(f)
+        singles.append(s.forward(f).clone())
+    for _ in range(2):  # second call replays the captured graph
+        outs = batch_forward(surfs, fields)
+        for a, b in zip(outs, singles):
+            torch.testing.assert_close(a, b, rtol=1e-12, atol=1e-12 * b.abs().max().item())
+    surfs[0].check()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_every_tile_config_agrees(dev, prec):
+    w = workload(1, scale=0.5)
+    from paper_2312_16263_gb300 import FWH
+    s = FWH.from_workload(w, prec)
+    f = w.fields(device=dev, dtype="float64" if prec == "fp64" else "float32")
+    ref = s.forward(f).clone()
+    from paper_2312_16263_gb300 import _abi
+    n = 5 if prec == "mixed" else 3
+    for i in range(n):
+        s.set_tile_config(i)
+        out = s.forward(f)
+        torch.testing.assert_close(out, ref, rtol=1e-6 if prec == "mixed" else 1e-12,
+                                   atol=1e-9 * ref.abs().max().item())
+    chosen = s.autotune(w.nt)
+    assert 0 <= chosen < n
+    s.check()
+    assert _abi.load() is not None
