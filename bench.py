@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the FW-H hot path on GB300: panel x source-step x observer
+evaluations per second for the 32768-panel x 2048-step x 72-observer convected
+dipole (sphere r=1.5, M0=0.5, AoA=10 deg, dt=0.01), mixed precision, with the
+plain FP64 form, the end-to-end C-ABI call on host buffers and the FP64 CPU
+oracle timed beside it.
+
+One step = one fwh_forward: integrand preparation + forward scatter over the
+whole surface, all 2048 source steps and all observers, inputs resident in
+HBM (1.34 GB of FP32 fields and 4.3 GB of prepared series: both larger than
+the 129 MB L2, so no flush is needed between steps).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own observer set (the circle rotated by a
+rank-dependent angle): the observer dimension is independent, so there is no
+data-path collective and the scaling is weak.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FW-H panel·τ·observer evals/s, mixed vs FP64 at ≤1e-4 rel L2; % roofline"
+UNIT = "evals/s"
+FLOP_PER_EVAL = 40          # 20 FMA: 8 + 8 (signal, spline moment) + 4 (interpolation)
+# FP32 FMA roof: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 FMA roof: nominal GB300 FP64 rate
+FP64_PEAK_TFLOPS = 1.25
+PROFILE = os.path.join(ROOT, "profiles", "forward_kernel_workload2.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_2312_16263_gb300", "csrc", "fwh_forward.cu")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_workload(rank: int, ws: int):
+    import numpy as np
+    from fwh_inputs import observers_circle, workload
+    w = workload(2)
+    if rank > 0:  # rotate the 72-observer circle: a distinct, equally sized set
+        ang = 2 * np.pi / 72 * rank / ws
+        c, s = np.cos(ang), np.sin(ang)
+        w.observers = observers_circle(100.0, 72) @ np.array([[c, s, 0], [-s, c, 0], [0, 0, 1]])
+    return w
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.idx = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        load = [v for v in sm if mx and v > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def profile_traffic():
+    """DRAM bytes per forward launch from the committed ncu summary, if that
+    summary was taken on the current kernel source (hash match), else None."""
+    if not os.path.exists(PROFILE):
+        return None
+    txt = open(PROFILE).read()
+    h = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != h:
+        return None
+    return float(t.group(1))
+
+
+def cpu_baseline(w, n_obs=4):
+    """The FP64 oracle as it stands, on all host cores, on 4 of the 72
+    observers of the same workload (all panels, all source steps)."""
+    import numpy as np
+    from oracle import Oracle
+    from oracle.oracle import max_threads
+    pick = np.linspace(0, w.observers.shape[0], n_obs, endpoint=False).astype(int)
+    f = w.fields("float32").double().numpy()
+    orc = Oracle.from_workload(w)
+    t0 = time.perf_counter()
+    p, ts, nv = orc.forward(f, w.observers[pick])
+    dt = time.perf_counter() - t0
+    evals = w.surface.n_panels * w.nt * len(pick)
+    return {"value": evals / dt, "unit": UNIT, "cores": max_threads(), "kind": "oracle",
+            "sample": f"observers {pick.tolist()} of 72, all {w.surface.n_panels} panels x "
+                      f"{w.nt} steps ({evals:.3g} evals, {dt:.1f} s)"}, (pick, p, nv)
+
+
+def rel_l2_stats(p_gpu, nv_gpu, p_ref, nv_ref, idx):
+    import numpy as np
+    errs = []
+    for k, o in enumerate(idx):
+        n = int(min(nv_gpu[o], nv_ref[k]))
+        ref = p_ref[k, :n]
+        errs.append(float(np.linalg.norm(p_gpu[o, :n] - ref) / np.linalg.norm(ref)))
+    return {"max": max(errs), "median": statistics.median(errs)}
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the FP64 CPU oracle (the paper ships no GPU code), timed
+    as it stands on the host cores, one bounded sample (one observer of the
+    same workload, all panels and steps) per step."""
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import Oracle
+    from oracle.oracle import max_threads
+    w = rank_workload(0, 1)
+    f = w.fields("float32").double().numpy()
+    orc = Oracle.from_workload(w)
+    evals = w.surface.n_panels * w.nt
+    for i in range(args.warmup):
+        orc.forward(f, w.observers[i % 72:i % 72 + 1])
+    times = []
+    for i in range(args.steps):
+        o = (7 * i) % 72
+        t0 = time.perf_counter()
+        orc.forward(f, w.observers[o:o + 1])
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = evals / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "panels": w.surface.n_panels, "nt": w.nt,
+                       "observers_per_step": 1, "sample": "one observer per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": max_threads(),
+                             "kind": "oracle", "sample": "1 of 72 observers per step, all "
+                             f"{w.surface.n_panels} panels x {w.nt} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import numpy as np
+    import torch
+
+    from __graft_entry__ import build
+    build()
+    from paper_2312_16263_gb300 import FWH
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = rank_workload(rank, ws)
+    evals = w.evals
+    s = FWH.from_workload(w, "mixed")
+    f = w.fields(device=dev, dtype="float32")
+    out = torch.empty((s.O, w.nt), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        s.forward(f, out)
+    torch.cuda.synchronize()
+    s.check()
+    s.set_timing(True)
+    s.timing_totals(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            s.forward(f, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+    ms_step = e0.elapsed_time(e1) / args.steps
+    tt = s.timing_totals(reset=True)
+    s.set_timing(False)
+    s.check()
+    ms_max = max_over_ranks(ms_step, ws)
+    value = evals * ws / (ms_max / 1e3)
+    fwd_ms = tt["forward_ms"] / max(1, tt["calls"])
+    prep_ms = tt["prep_ms"] / max(1, tt["calls"])
+    achieved = evals * FLOP_PER_EVAL / (fwd_ms / 1e3) / 1e12
+    traffic = profile_traffic()
+    p_mixed = out.cpu().numpy()
+    _, nv = s.window(w.nt)
+
+    # plain FP64 form on the same workload
+    s64 = FWH.from_workload(w, "fp64")
+    f64 = f.double()
+    out64 = torch.empty_like(out)
+    s64.forward(f64, out64)
+    torch.cuda.synchronize()
+    s64.set_timing(True)
+    s64.timing_totals(reset=True)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(args.fp64_steps):
+        s64.forward(f64, out64)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = a0.elapsed_time(a1) / args.fp64_steps
+    tt64 = s64.timing_totals(reset=True)
+    fwd64 = tt64["forward_ms"] / max(1, tt64["calls"])
+    p64 = out64.cpu().numpy()
+    s64.check()
+    den = np.linalg.norm(p64, axis=1)
+    rel_mixed_fp64 = np.linalg.norm(p_mixed - p64, axis=1) / np.where(den > 0, den, 1)
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    fh = f.cpu().pin_memory()
+    oh = torch.empty((s.O, w.nt), dtype=torch.float64).pin_memory()
+    s.forward(fh, oh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        s.forward(fh, oh)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_ms_max = max_over_ranks(e2e_s * 1e3, ws)
+    assert torch.equal(oh, out.cpu()) or np.allclose(oh.numpy(), p_mixed, rtol=0,
+                                                     atol=1e-12 * np.abs(p_mixed).max())
+    clocks = clk.summary()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (analytic convected x1-dipole, A=0.01, omega=4 pi)",
+        "config": {"workload": w.name, "panels": w.surface.n_panels, "nt": w.nt,
+                   "observers_per_gpu": s.O, "precision": "mixed (FP32 series and integrand "
+                   "arithmetic, FP64 arrival times/weights and output)",
+                   "l2": "inputs larger than L2 (1.34 GB fields, 4.3 GB series per step)",
+                   "parallelism": f"observer sets x{ws}, no collective"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": traffic,
+                     "kernel": "k_forward (forward scatter)",
+                     "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "kernel_ms": fwd_ms, "prep_ms": prep_ms,
+                     "flop_per_eval": FLOP_PER_EVAL},
+        "fp64": {"value": evals * ws / (max_over_ranks(ms64, ws) / 1e3), "unit": UNIT,
+                 "ms_per_step": ms64, "kernel_ms": fwd64,
+                 "achieved_tflops": evals * FLOP_PER_EVAL / (fwd64 / 1e3) / 1e12,
+                 "peak_tflops": FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64"},
+        "accuracy": {"mixed_vs_fp64_rel_l2_max": float(rel_mixed_fp64.max()),
+                     "mixed_vs_fp64_rel_l2_median": float(np.median(rel_mixed_fp64))},
+        "e2e": {"value": evals * ws / (e2e_ms_max / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(fh.numel() * fh.element_size()),
+                "d2h_bytes_per_step": int(oh.numel() * oh.element_size()),
+                "ms_per_step": e2e_ms_max},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb, (pick, p_ref, nv_ref) = cpu_baseline(w)
+        line["cpu_baseline"] = cb
+        line["accuracy"]["mixed_vs_oracle_rel_l2"] = rel_l2_stats(p_mixed, nv, p_ref, nv_ref, pick)
+        line["accuracy"]["fp64_vs_oracle_rel_l2"] = rel_l2_stats(p64, nv, p_ref, nv_ref, pick)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    s64.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

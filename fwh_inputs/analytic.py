@@ -183,7 +183,7 @@ def wave_equation_residual(x: np.ndarray, flow: FlowCase, amplitude: float, omeg
 def time_series(amp: np.ndarray, omega: float, t: np.ndarray) -> np.ndarray:
     """Re(exp(i omega t) amp) for amp [N, C] -> [nt, C, N] float64."""
     e = np.exp(1j * omega * np.asarray(t, dtype=np.float64))
-    return np.real(e[:, None, None] * amp.T[None, :, :])
+    return np.ascontiguousarray(np.real(e[:, None, None] * amp.T[None, :, :]))
 
 
 def surface_fields(kind: str, centroids: np.ndarray, flow: FlowCase, amplitude: float,

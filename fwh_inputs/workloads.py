@@ -68,7 +68,7 @@ class Workload:
         if self.fields_kind in ("monopole", "dipole"):
             f = surface_fields(self.fields_kind, self.surface.centroids, self.flow,
                                self.amplitude, self.omega, self.dt, nt, self.axis)
-            return torch.as_tensor(f, dtype=tdt, device=device)
+            return torch.as_tensor(f, dtype=tdt, device=device).contiguous()
         from .broadband import broadband_fields
         return broadband_fields(self.surface.centroids, self.mach, self.dt, nt,
                                 self.seed, device=device, dtype=tdt)

@@ -145,13 +145,16 @@ fwh_status fwh_autotune(fwh_handle h, int64_t nt, int *chosen, void *stream);
 fwh_status fwh_set_tile_config(fwh_handle h, int config);
 
 /*
- * Device times (milliseconds, CUDA events on the launching stream) of the
- * last fwh_forward on this handle: [0] integrand preparation, [1] the
- * forward scatter kernel, [2] the whole call.  Recording is enabled by
- * fwh_set_timing(h, 1) and costs two event records per kernel.
+ * Device times (milliseconds, CUDA events recorded on the launching stream,
+ * never synchronised by the forward call itself) of fwh_forward calls made
+ * while fwh_set_timing(h, 1) is on: [0] integrand preparation, [1] the
+ * forward scatter kernel, [2] the whole call.  fwh_last_timings gives the
+ * last call; fwh_timing_totals the sums over all timed calls since the last
+ * reset and their count.  Both synchronise on the recorded events.
  */
 fwh_status fwh_set_timing(fwh_handle h, int enable);
 fwh_status fwh_last_timings(fwh_handle h, float *ms3);
+fwh_status fwh_timing_totals(fwh_handle h, double *ms3, int64_t *calls, int reset);
 
 /*
  * Synchronise `stream` and report the device-side checks raised by this

@@ -133,6 +133,13 @@ class FWH:
         _abi.check(self.lib.fwh_last_timings(self.h, ms), self.h)
         return {"prep_ms": ms[0], "forward_ms": ms[1], "total_ms": ms[2]}
 
+    def timing_totals(self, reset: bool = True):
+        ms = (ctypes.c_double * 3)()
+        n = ctypes.c_int64(0)
+        _abi.check(self.lib.fwh_timing_totals(self.h, ms, ctypes.byref(n), int(bool(reset))),
+                   self.h)
+        return {"prep_ms": ms[0], "forward_ms": ms[1], "total_ms": ms[2], "calls": int(n.value)}
+
     def check(self, stream=None):
         _abi.check(self.lib.fwh_check(self.h, _stream_ptr(stream)), self.h)
 

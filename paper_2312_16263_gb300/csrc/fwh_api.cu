@@ -74,6 +74,11 @@ struct fwh_ctx {
   bool timing = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   float last_ms[3] = {0, 0, 0};
+  // timing pool: one (start, after-prep, end) triple per timed call
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+  double sum_ms[3] = {0, 0, 0};
+  int64_t sum_calls = 0;
   std::string err;
   // batch
   std::map<std::vector<uintptr_t>, Graph> graphs;
@@ -241,7 +246,19 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
   const FwdConfig c = fwd_config(fp64, cfg);
   fwh_status st = plan(h, c);
   if (st != FWH_OK) return st;
-  if (h->timing) CK(h, cudaEventRecord(h->ev[0], s));
+  cudaEvent_t *tev = nullptr;
+  if (h->timing) {
+    if (h->pool_used + 3 > h->pool.size()) {
+      for (int i = 0; i < 3 * 64; ++i) {
+        cudaEvent_t e;
+        CK(h, cudaEventCreate(&e));
+        h->pool.push_back(e);
+      }
+    }
+    tev = &h->pool[h->pool_used];
+    h->pool_used += 3;
+    CK(h, cudaEventRecord(tev[0], s));
+  }
   CK(h, cudaMemsetAsync(d_pout, 0, (size_t)h->O * h->nt * sizeof(double), s));
   PrepArgs<T> pa{};
   pa.fields = d_fields;
@@ -255,7 +272,7 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
   pa.sa = h->sa;
   pa.dt = h->dt;
   CK(h, launch_prep<T>(pa, s));
-  if (h->timing) CK(h, cudaEventRecord(h->ev[1], s));
+  if (tev) CK(h, cudaEventRecord(tev[1], s));
   FwdArgs<T> fa{};
   fa.X = pa.X;
   fa.coef = reinterpret_cast<const T *>(h->coef.p);
@@ -272,13 +289,7 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
   fa.n_segs = (h->ntp + fa.seg_len - 1) / fa.seg_len;
   fa.win = c.win;
   CK(h, launch_forward<T>(fa, cfg, s));
-  if (h->timing) {
-    CK(h, cudaEventRecord(h->ev[2], s));
-    CK(h, cudaEventSynchronize(h->ev[2]));
-    cudaEventElapsedTime(&h->last_ms[0], h->ev[0], h->ev[1]);
-    cudaEventElapsedTime(&h->last_ms[1], h->ev[1], h->ev[2]);
-    cudaEventElapsedTime(&h->last_ms[2], h->ev[0], h->ev[2]);
-  }
+  if (tev) CK(h, cudaEventRecord(tev[2], s));
   return FWH_OK;
 }
 
@@ -292,6 +303,27 @@ void drop_graphs(fwh_handle h) {
     release(kv.second.counter);
   }
   h->bplans.clear();
+}
+
+// Resolve every recorded timing triple (synchronising on the last one).
+fwh_status drain_timings(fwh_handle h) {
+  for (size_t i = 0; i + 3 <= h->pool_used; i += 3) {
+    cudaEvent_t *t = &h->pool[i];
+    CK(h, cudaEventSynchronize(t[2]));
+    float a = 0, b = 0, c = 0;
+    CK(h, cudaEventElapsedTime(&a, t[0], t[1]));
+    CK(h, cudaEventElapsedTime(&b, t[1], t[2]));
+    CK(h, cudaEventElapsedTime(&c, t[0], t[2]));
+    h->last_ms[0] = a;
+    h->last_ms[1] = b;
+    h->last_ms[2] = c;
+    h->sum_ms[0] += a;
+    h->sum_ms[1] += b;
+    h->sum_ms[2] += c;
+    h->sum_calls += 1;
+  }
+  h->pool_used = 0;
+  return FWH_OK;
 }
 
 fwh_status check_device_flag(fwh_handle h, cudaStream_t s) {
@@ -639,6 +671,8 @@ fwh_status fwh_autotune(fwh_handle h, int64_t nt, int *chosen, void *stream) {
                : run_forward<float>(h, reinterpret_cast<const float *>(f.p),
                                     reinterpret_cast<double *>(po.p), s);
       if (st != FWH_OK) break;
+      st = drain_timings(h);
+      if (st != FWH_OK) break;
       if (rep > 0) tot += h->last_ms[1];
     }
     if (st != FWH_OK) {
@@ -667,7 +701,22 @@ fwh_status fwh_set_timing(fwh_handle h, int enable) {
 
 fwh_status fwh_last_timings(fwh_handle h, float *ms3) {
   if (!h || !ms3) return fail(h, FWH_ERR_ARG, "NULL argument");
+  fwh_status st = drain_timings(h);
+  if (st != FWH_OK) return st;
   for (int i = 0; i < 3; ++i) ms3[i] = h->last_ms[i];
+  return FWH_OK;
+}
+
+fwh_status fwh_timing_totals(fwh_handle h, double *ms3, int64_t *calls, int reset) {
+  if (!h || !ms3) return fail(h, FWH_ERR_ARG, "NULL argument");
+  fwh_status st = drain_timings(h);
+  if (st != FWH_OK) return st;
+  for (int i = 0; i < 3; ++i) ms3[i] = h->sum_ms[i];
+  if (calls) *calls = h->sum_calls;
+  if (reset) {
+    h->sum_ms[0] = h->sum_ms[1] = h->sum_ms[2] = 0;
+    h->sum_calls = 0;
+  }
   return FWH_OK;
 }
 
@@ -697,6 +746,7 @@ void fwh_destroy(fwh_handle h) {
     release(*b);
   for (int i = 0; i < 4; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   for (int i = 0; i < 2; ++i)
     if (h->bev[i]) cudaEventDestroy(h->bev[i]);
   if (h->side) cudaStreamDestroy(h->side);

@@ -187,8 +187,10 @@ def test_every_tile_config_agrees(dev, prec):
     for i in range(n):
         s.set_tile_config(i)
         out = s.forward(f)
-        torch.testing.assert_close(out, ref, rtol=1e-6 if prec == "mixed" else 1e-12,
-                                   atol=1e-9 * ref.abs().max().item())
+        # FP32 sums in a different order: compare on the signal's scale
+        torch.testing.assert_close(out, ref, rtol=0,
+                                   atol=(1e-6 if prec == "mixed" else 1e-12) *
+                                   ref.abs().max().item())
     chosen = s.autotune(w.nt)
     assert 0 <= chosen < n
     s.check()
