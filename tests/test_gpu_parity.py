@@ -8,6 +8,8 @@ counts that are not multiples of the 16-panel prep tile or the 64-panel set,
 record lengths that are not multiples of the 128-sample chunk, one observer,
 unstructured (Morton-ordered) geometry, high Mach and negative AoA.
 """
+import zlib
+
 import numpy as np
 import pytest
 import torch
@@ -77,7 +79,7 @@ def test_workload1_parity(dev, prec):
 @pytest.mark.parametrize("case", ["ragged", "min_nt", "one_obs", "unstructured", "high_mach",
                                   "many_obs"])
 def test_edge_cases(dev, prec, case):
-    rng = np.random.default_rng(abs(hash(case)) % 2**32)
+    rng = np.random.default_rng(zlib.crc32(case.encode()))
     mach, aoa, dt = 0.35, -12 * DEG, 0.03
     surf = uv_sphere(1.0, 7, 11)          # 77 panels: ragged vs 16/64
     nt = 301                              # ragged vs the 128-sample chunk
