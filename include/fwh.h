@@ -164,6 +164,28 @@ fwh_status fwh_timing_totals(fwh_handle h, double *ms3, int64_t *calls, int rese
  */
 fwh_status fwh_check(fwh_handle h, void *stream);
 
+/*
+ * Forward pass that allocates no device memory.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc/cudaFree
+ * or any allocator while they run (a real-time loop with a memory budget
+ * fixed up front, a host callback, code embedded in a framework that owns
+ * the device memory and forbids allocation during a step).  Results equal
+ * fwh_forward's.  The handle must have been set up earlier (fwh_create and
+ * fwh_set_observers allocate); fields and p_out must be device pointers
+ * (FWH_ERR_ARG otherwise: there is no staging).
+ * Scratch: the prepared series and per-call tables live in one file-scope
+ * device array of 64 MiB that every GPU loading the library reserves until
+ * the process exits; a problem needing more (about P x round_up(nt, 128) x
+ * 64 bytes for FWH_MIXED, x 128 for FWH_FP64) is rejected with FWH_ERR_ARG
+ * and a message giving both sizes.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls on a
+ * device share the array (each call writes everything it reads), so calls
+ * whose GPU work overlaps race and must be serialised by the caller.
+ */
+fwh_status fwh_forward_noalloc(fwh_handle h, const void *fields, int64_t nt, double *p_out,
+                               void *stream);
+
 /* Number of panels, observers and the precision of a handle. */
 fwh_status fwh_get_sizes(fwh_handle h, int64_t *n_panels, int64_t *n_obs,
                          int *precision);

@@ -29,6 +29,7 @@ SIGNATURES = {
                                   ctypes.c_int]),
     "fwh_set_observers": (ctypes.c_int, [_vp, _i64, _vp]),
     "fwh_forward": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    "fwh_forward_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "fwh_observer_window": (ctypes.c_int, [_vp, _i64, _dp, _ip64]),
     "fwh_backward": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "fwh_batch_forward": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp),

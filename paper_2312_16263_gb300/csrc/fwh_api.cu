@@ -912,3 +912,103 @@ extern "C" fwh_status fwh_check(fwh_handle h, void *stream) {
   if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
   return check_device_flag(h, reinterpret_cast<cudaStream_t>(stream));
 }
+
+// ---------------------------------------------------------------------------
+// Forward pass into caller-provided device scratch (no device allocation).
+// Used by the static-scratch entry point in fwh_noalloc.cu.  Every byte of
+// the scratch that this call reads is written earlier in the same call:
+// observer windows and panel sets are copied in, every row of the prepared
+// series (including the zero rows past nt) is written by the prep kernel.
+// ---------------------------------------------------------------------------
+namespace {
+
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+template <typename T>
+fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, double *d_pout,
+                                  cudaStream_t s, unsigned char *scratch, size_t cap) {
+  const bool fp64 = sizeof(T) == 8;
+  const int cfg = h->cfg >= 0 ? h->cfg : default_cfg(h);
+  const FwdConfig c = fwd_config(fp64, cfg);
+  // observer window (Eqs. t_start, t_end), as prepare_nt but into host temporaries
+  std::vector<int> nv(h->O);
+  const double tau_max = (double)(nt - 1) * h->dt;
+  for (int64_t o = 0; o < h->O; ++o) {
+    const double ts = h->mach * h->Rmax[o];
+    const double te = tau_max + h->mach * h->Rmin[o];
+    double v = std::floor((te - ts) / h->dt) + 1.0;
+    nv[o] = (int)std::max(0.0, std::min((double)nt, v));
+  }
+  const std::vector<int> sets = build_sets(h->y, h->P, h->mach, h->dt, c.win - 32 * c.tk - 1);
+  const int ntp = (int)((nt + 127) / 128 * 128);
+  const size_t off_sets = round256((size_t)h->O * sizeof(int));
+  const size_t off_x = off_sets + round256(sets.size() * sizeof(int));
+  const size_t need = off_x + (size_t)h->P * ntp * kRec * sizeof(T);
+  if (need > cap)
+    return fail(h, FWH_ERR_ARG,
+                "problem needs " + std::to_string(need) + " bytes of scratch (panels x nt rounded "
+                "up to 128 x 16 values + windows); the static scratch holds " +
+                    std::to_string(cap) + " bytes");
+  int *d_nv = reinterpret_cast<int *>(scratch);
+  int *d_sets = reinterpret_cast<int *>(scratch + off_sets);
+  T *d_X = reinterpret_cast<T *>(scratch + off_x);
+  CK(h, cudaMemcpyAsync(d_nv, nv.data(), nv.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(h, cudaMemcpyAsync(d_sets, sets.data(), sets.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        s));
+  CK(h, cudaMemsetAsync(d_pout, 0, (size_t)h->O * nt * sizeof(double), s));
+  PrepArgs<T> pa{};
+  pa.fields = d_fields;
+  pa.perm = h->identity ? nullptr : h->d_perm;
+  pa.n = h->d_n;
+  pa.X = d_X;
+  pa.P = (int)h->P;
+  pa.nt = (int)nt;
+  pa.ntp = ntp;
+  pa.ca = h->ca;
+  pa.sa = h->sa;
+  pa.dt = h->dt;
+  CK(h, launch_prep<T>(pa, s));
+  FwdArgs<T> fa{};
+  fa.X = d_X;
+  fa.coef = reinterpret_cast<const T *>(h->coef.p);
+  fa.p_out = d_pout;
+  fa.n_valid = d_nv;
+  fa.set_begin = d_sets;
+  fa.err = h->d_err;
+  fa.nsets = (int)sets.size() - 1;
+  fa.O = (int)h->O;
+  fa.ntp = ntp;
+  fa.nt = (int)nt;
+  obs_tiling(h, c, &fa.obs_per_cta, &fa.n_obs_groups);
+  fa.seg_len = c.seg_chunks * 32 * c.tk;
+  fa.n_segs = (ntp + fa.seg_len - 1) / fa.seg_len;
+  fa.win = c.win;
+  CK(h, launch_forward<T>(fa, cfg, s));
+  return FWH_OK;
+}
+
+}  // namespace
+
+fwh_status fwh_forward_into_scratch(fwh_handle h, const void *fields, int64_t nt,
+                                    double *p_out, cudaStream_t s, void *scratch,
+                                    size_t cap) {
+  if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
+  if (h->O < 1) return fail(h, FWH_ERR_STATE, "fwh_set_observers must come first");
+  if (!fields || !p_out) return fail(h, FWH_ERR_ARG, "fields or p_out is NULL");
+  if (nt < 3 || nt > (int64_t)1 << 28) return fail(h, FWH_ERR_ARG, "nt must be >= 3");
+  if (!scratch) return fail(h, FWH_ERR_ARG, "scratch is NULL");
+  if (!is_device_ptr(fields) || !is_device_ptr(p_out))
+    return fail(h, FWH_ERR_ARG, "this entry point takes device buffers only (no staging)");
+  return h->precision == FWH_FP64
+             ? forward_into_scratch_t<double>(h, reinterpret_cast<const double *>(fields), nt,
+                                              p_out, s, static_cast<unsigned char *>(scratch),
+                                              cap)
+             : forward_into_scratch_t<float>(h, reinterpret_cast<const float *>(fields), nt,
+                                             p_out, s, static_cast<unsigned char *>(scratch),
+                                             cap);
+}
+
+// Record an error on a handle from another translation unit of the library.
+fwh_status fwh_fail_handle(fwh_handle h, fwh_status st, const char *msg) {
+  return fail(h, st, msg);
+}
