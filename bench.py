@@ -51,7 +51,35 @@ def parse_args():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="small case for ncu: workload 2 with --nt steps, two forward calls")
+    ap.add_argument("--nt", type=int, default=512)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--tile-config", type=int, default=-1,
+                    help="forward tile configuration index (-1: the library default)")
     return ap.parse_args()
+
+
+def profile_case(args):
+    """Two fwh_forward calls on workload 2 cut to --nt source steps (about
+    1.4 GB on the device at nt=512): the capture target for ncu --set full."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    from paper_2312_16263_gb300 import FWH
+    w = rank_workload(0, 1)
+    w.nt = args.nt
+    s = FWH.from_workload(w, args.precision)
+    if args.tile_config >= 0:
+        s.set_tile_config(args.tile_config)
+    f = w.fields(device="cuda:0", dtype="float32" if args.precision == "mixed" else "float64")
+    out = torch.empty((s.O, w.nt), dtype=torch.float64, device="cuda:0")
+    for _ in range(2):
+        s.forward(f, out)
+    torch.cuda.synchronize()
+    s.check()
+    print(json.dumps({"profile_case": w.name, "nt": w.nt, "precision": args.precision,
+                      "max_abs": float(out.abs().max())}))
 
 
 def dist_setup():
@@ -232,6 +260,9 @@ def run_reference(args, ws, rank):
 
 def main():
     args = parse_args()
+    if args.profile_case:
+        profile_case(args)
+        return
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)

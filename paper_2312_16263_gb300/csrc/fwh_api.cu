@@ -61,7 +61,10 @@ struct fwh_ctx {
   double *d_y = nullptr, *d_n = nullptr, *d_dS = nullptr, *d_x = nullptr;
   double *d_Rmax = nullptr, *d_Rmin = nullptr;
   int *d_perm = nullptr, *d_err = nullptr;
-  Buf coef, X, G, nvalid, sets, stage_in, stage_out, stage_grad;
+  Buf coef, X, G, nvalid, sets, stage_in, stage_out, stage_grad, tmap, imax;
+  const void *tmap_X = nullptr;  // X buffer / rows / box the device descriptor describes
+  int tmap_box = 0;
+  long long tmap_rows = 0;
   // per-nt
   int64_t nt = -1;
   int ntp = 0;
@@ -201,20 +204,33 @@ void obs_tiling(const fwh_ctx *h, const FwdConfig &c, int *obs_per_cta, int *gro
   *groups = (int)((h->O + *obs_per_cta - 1) / *obs_per_cta);
 }
 
-fwh_status plan(fwh_handle h, const FwdConfig &c) {
+// Panel sets for a config, and the plan kernel's per-(set, observer) shift
+// table and per-record window offsets, enqueued on `s`.
+fwh_status plan(fwh_handle h, const FwdConfig &c, cudaStream_t s) {
   const int ch = 32 * c.tk;
   if (h->plan_win == c.win && h->plan_ch == ch) return FWH_OK;
   const int smax = c.win - ch - 1;
   h->set_begin = build_sets(h->y, h->P, h->mach, h->dt, smax);
-  h->plan_win = c.win;
-  h->plan_ch = ch;
   const size_t bytes = h->set_begin.size() * sizeof(int);
+  const int nsets = (int)h->set_begin.size() - 1;
   CK(h, ensure(h->sets, bytes));
   CK(h, cudaMemcpy(h->sets.p, h->set_begin.data(), bytes, cudaMemcpyHostToDevice));
+  CK(h, ensure(h->imax, (size_t)nsets * h->O * sizeof(int)));
+  if (h->precision == FWH_FP64)
+    CK(h, launch_plan<double>(reinterpret_cast<double *>(h->coef.p),
+                              reinterpret_cast<const int *>(h->sets.p), nsets, (int)h->O, smax,
+                              reinterpret_cast<int *>(h->imax.p), h->d_err, s));
+  else
+    CK(h, launch_plan<float>(reinterpret_cast<float *>(h->coef.p),
+                             reinterpret_cast<const int *>(h->sets.p), nsets, (int)h->O, smax,
+                             reinterpret_cast<int *>(h->imax.p), h->d_err, s));
+  h->plan_win = c.win;
+  h->plan_ch = ch;
   return FWH_OK;
 }
 
-// Per-nt window and workspace.  ntp is a multiple of 128 (every chunk size).
+// Per-nt window and workspace.  ntp is a multiple of 256, hence of every
+// forward chunk (32 x TK samples) and prep chunk.
 fwh_status prepare_nt(fwh_handle h, int64_t nt) {
   if (h->nt != nt) {
     h->h_nvalid.assign(h->O, 0);
@@ -231,20 +247,58 @@ fwh_status prepare_nt(fwh_handle h, int64_t nt) {
     CK(h, ensure(h->nvalid, h->O * sizeof(int)));
     CK(h, cudaMemcpy(h->nvalid.p, h->h_nvalid.data(), h->O * sizeof(int),
                      cudaMemcpyHostToDevice));
+    const int64_t ntp = (nt + 255) / 256 * 256;  // a multiple of every chunk length
+    if (h->precision == FWH_MIXED && h->P * ntp >= ((int64_t)1 << 32))
+      return fail(h, FWH_ERR_ARG, "panels x padded steps must stay below 2^32 per handle");
     h->nt = nt;
-    h->ntp = (int)((nt + 127) / 128 * 128);
+    h->ntp = (int)ntp;
   }
   const size_t ts = tsize(h->precision);
   CK(h, ensure(h->X, (size_t)h->P * h->ntp * kRec * ts));
   return FWH_OK;
 }
 
+// Config actually used: TMA configs address X rows with 32-bit coordinates
+// (FP64 falls back to a direct-load shape; every FP32 shape is a TMA shape,
+// its rows are sample pairs, and prepare_nt bounds P x ntp below 2^32).
+int effective_cfg(const fwh_ctx *h, int64_t ntp) {
+  const bool fp64 = h->precision == FWH_FP64;
+  int cfg = h->cfg >= 0 ? h->cfg : default_cfg(h);
+  if (fwd_config(fp64, cfg).pipe == 1 && h->P * ntp >= ((int64_t)1 << 31)) {
+    for (int i = 0; i < fwd_num_configs(fp64); ++i)
+      if (fwd_config(fp64, i).pipe == 0) return i;
+  }
+  return cfg;
+}
+
+// Device-resident TMA descriptor of the handle's X buffer (re-encoded when
+// the buffer, its row count or the box changes).
+fwh_status ensure_tmap(fwh_handle h, int box_rows) {
+  const long long rows = (long long)h->P * h->ntp;
+  if (h->tmap.p && h->tmap_X == h->X.p && h->tmap_rows == rows && h->tmap_box == box_rows)
+    return FWH_OK;
+  alignas(64) unsigned char desc[128];
+  if (!encode_x_tensor_map(desc, h->X.p, (unsigned long long)rows,
+                           h->precision == FWH_FP64, box_rows))
+    return fail(h, FWH_ERR_CUDA, "cuTensorMapEncodeTiled refused the series layout");
+  CK(h, ensure(h->tmap, 128));
+  CK(h, cudaMemcpy(h->tmap.p, desc, 128, cudaMemcpyHostToDevice));
+  h->tmap_X = h->X.p;
+  h->tmap_rows = rows;
+  h->tmap_box = box_rows;
+  return FWH_OK;
+}
+
 template <typename T>
 fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStream_t s) {
   const bool fp64 = sizeof(T) == 8;
-  const int cfg = h->cfg >= 0 ? h->cfg : default_cfg(h);
+  const int cfg = effective_cfg(h, h->ntp);
   const FwdConfig c = fwd_config(fp64, cfg);
-  fwh_status st = plan(h, c);
+  if (c.pipe == 1) {
+    fwh_status st0 = ensure_tmap(h, 32 * c.tk);
+    if (st0 != FWH_OK) return st0;
+  }
+  fwh_status st = plan(h, c, s);
   if (st != FWH_OK) return st;
   cudaEvent_t *tev = nullptr;
   if (h->timing) {
@@ -274,11 +328,13 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
   CK(h, launch_prep<T>(pa, s));
   if (tev) CK(h, cudaEventRecord(tev[1], s));
   FwdArgs<T> fa{};
+  fa.tmX = h->tmap.p;
   fa.X = pa.X;
   fa.coef = reinterpret_cast<const T *>(h->coef.p);
   fa.p_out = d_pout;
   fa.n_valid = reinterpret_cast<const int *>(h->nvalid.p);
   fa.set_begin = reinterpret_cast<const int *>(h->sets.p);
+  fa.i0max_tab = reinterpret_cast<const int *>(h->imax.p);
   fa.err = h->d_err;
   fa.nsets = (int)h->set_begin.size() - 1;
   fa.O = (int)h->O;
@@ -516,7 +572,8 @@ fwh_status fwh_set_observers(fwh_handle h, int64_t O, const double *xyz) {
   CK(h, cudaMemcpy(h->Rmin.data(), h->d_Rmin, O * sizeof(double), cudaMemcpyDeviceToHost));
   h->xobs = x;
   h->O = O;
-  h->nt = -1;  // window depends on the observers
+  h->nt = -1;         // window depends on the observers
+  h->plan_win = -1;   // records were rewritten: window offsets must be re-planned
   drop_graphs(h);
   return FWH_OK;
 }
@@ -742,7 +799,7 @@ void fwh_destroy(fwh_handle h) {
   if (h->d_perm) cudaFree(h->d_perm);
   if (h->d_err) cudaFree(h->d_err);
   for (Buf *b : {&h->coef, &h->X, &h->G, &h->nvalid, &h->sets, &h->stage_in, &h->stage_out,
-                 &h->stage_grad})
+                 &h->stage_grad, &h->tmap, &h->imax})
     release(*b);
   for (int i = 0; i < 4; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
@@ -768,20 +825,31 @@ template <typename T>
 fwh_status batch_build(int n, const fwh_handle *hs, const void *const *fields,
                        double *const *p_out, fwh_handle h0, BatchPlan &bp) {
   const bool fp64 = sizeof(T) == 8;
-  const int cfg = h0->cfg >= 0 ? h0->cfg : default_cfg(h0);
+  int cfg = h0->cfg >= 0 ? h0->cfg : default_cfg(h0);
+  for (int i = 0; i < n; ++i) {
+    const int ci = effective_cfg(hs[i], hs[i]->ntp);
+    if (fwd_config(fp64, ci).pipe != fwd_config(fp64, cfg).pipe) cfg = ci;
+  }
   const FwdConfig c = fwd_config(fp64, cfg);
   std::vector<FwdArgs<T>> args(n);
   std::vector<int> prefix(n + 1, 0);
   for (int i = 0; i < n; ++i) {
     fwh_handle h = hs[i];
-    fwh_status st = plan(h, c);
+    fwh_status st = plan(h, c, h0->side);
     if (st != FWH_OK) return fail(h0, st, h->err);
+    CK(h0, cudaStreamSynchronize(h0->side));
+    if (c.pipe == 1) {
+      st = ensure_tmap(h, 32 * c.tk);
+      if (st != FWH_OK) return fail(h0, st, h->err);
+    }
     FwdArgs<T> &fa = args[i];
+    fa.tmX = h->tmap.p;
     fa.X = reinterpret_cast<const T *>(h->X.p);
     fa.coef = reinterpret_cast<const T *>(h->coef.p);
     fa.p_out = p_out[i];
     fa.n_valid = reinterpret_cast<const int *>(h->nvalid.p);
     fa.set_begin = reinterpret_cast<const int *>(h->sets.p);
+    fa.i0max_tab = reinterpret_cast<const int *>(h->imax.p);
     fa.err = h0->d_err;
     fa.nsets = (int)h->set_begin.size() - 1;
     fa.O = (int)h->O;
@@ -868,6 +936,7 @@ extern "C" fwh_status fwh_batch_forward(int n, const fwh_handle *hs, const void 
     key.push_back((uintptr_t)hs[i]->O);
     key.push_back((uintptr_t)hs[i]->nvalid.p);
     key.push_back((uintptr_t)hs[i]->sets.p);
+    key.push_back((uintptr_t)hs[i]->imax.p);
   }
   key.push_back((uintptr_t)(h0->cfg + 1));
   if (!h0->side) {
@@ -928,7 +997,8 @@ template <typename T>
 fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, double *d_pout,
                                   cudaStream_t s, unsigned char *scratch, size_t cap) {
   const bool fp64 = sizeof(T) == 8;
-  const int cfg = h->cfg >= 0 ? h->cfg : default_cfg(h);
+  const int ntp0 = (int)((nt + 255) / 256 * 256);
+  const int cfg = effective_cfg(h, ntp0);
   const FwdConfig c = fwd_config(fp64, cfg);
   // observer window (Eqs. t_start, t_end), as prepare_nt but into host temporaries
   std::vector<int> nv(h->O);
@@ -941,8 +1011,11 @@ fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, d
   }
   const std::vector<int> sets = build_sets(h->y, h->P, h->mach, h->dt, c.win - 32 * c.tk - 1);
   const int ntp = (int)((nt + 127) / 128 * 128);
-  const size_t off_sets = round256((size_t)h->O * sizeof(int));
-  const size_t off_x = off_sets + round256(sets.size() * sizeof(int));
+  const int nsets = (int)sets.size() - 1;
+  const size_t off_tm = round256((size_t)h->O * sizeof(int));
+  const size_t off_sets = off_tm + 256;
+  const size_t off_imax = off_sets + round256(sets.size() * sizeof(int));
+  const size_t off_x = (off_imax + round256((size_t)nsets * h->O * sizeof(int)) + 1023) / 1024 * 1024;
   const size_t need = off_x + (size_t)h->P * ntp * kRec * sizeof(T);
   if (need > cap)
     return fail(h, FWH_ERR_ARG,
@@ -951,10 +1024,22 @@ fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, d
                     std::to_string(cap) + " bytes");
   int *d_nv = reinterpret_cast<int *>(scratch);
   int *d_sets = reinterpret_cast<int *>(scratch + off_sets);
+  int *d_imax = reinterpret_cast<int *>(scratch + off_imax);
   T *d_X = reinterpret_cast<T *>(scratch + off_x);
   CK(h, cudaMemcpyAsync(d_nv, nv.data(), nv.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   CK(h, cudaMemcpyAsync(d_sets, sets.data(), sets.size() * sizeof(int), cudaMemcpyHostToDevice,
                         s));
+  if (c.pipe == 1) {
+    alignas(64) unsigned char desc[128];
+    if (!encode_x_tensor_map(desc, d_X, (unsigned long long)h->P * ntp, fp64, 32 * c.tk))
+      return fail(h, FWH_ERR_CUDA, "cuTensorMapEncodeTiled refused the series layout");
+    CK(h, cudaMemcpyAsync(scratch + off_tm, desc, 128, cudaMemcpyHostToDevice, s));
+  }
+  // window offsets of this plan (the handle's records get the same values a
+  // regular call with this configuration writes)
+  CK(h, launch_plan<T>(reinterpret_cast<T *>(h->coef.p), d_sets, nsets, (int)h->O,
+                       c.win - 32 * c.tk - 1, d_imax, h->d_err, s));
+  h->plan_win = -1;  // the handle's own set table may belong to another plan
   CK(h, cudaMemsetAsync(d_pout, 0, (size_t)h->O * nt * sizeof(double), s));
   PrepArgs<T> pa{};
   pa.fields = d_fields;
@@ -969,11 +1054,13 @@ fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, d
   pa.dt = h->dt;
   CK(h, launch_prep<T>(pa, s));
   FwdArgs<T> fa{};
+  fa.tmX = scratch + off_tm;
   fa.X = d_X;
   fa.coef = reinterpret_cast<const T *>(h->coef.p);
   fa.p_out = d_pout;
   fa.n_valid = d_nv;
   fa.set_begin = d_sets;
+  fa.i0max_tab = d_imax;
   fa.err = h->d_err;
   fa.nsets = (int)sets.size() - 1;
   fa.O = (int)h->O;

@@ -12,21 +12,38 @@
 // bin j (Eq. tau2), summed over panels.  20 FMA per (panel, sample, observer).
 //
 // Work item = (panel set, observer group, time segment).  A CTA holds NW
-// warps; warp w owns observers o_begin + w + NW m (m < obs_per_warp) of the
-// group and keeps, per observer, a window of `win` bins in shared memory.
-// Lanes map to source samples (k = k0 + lane + 32 j, j < TK), so each X row
-// is loaded once per warp and reused for all of the warp's observers, the
-// coefficient record is a warp-uniform broadcast, and the window updates are
-// conflict-free (consecutive lanes, consecutive bins).  The per-(p, o) shift
-// only moves the window offset, never the lane pattern.  After each chunk of
-// 32 TK samples the oldest 32 TK bins of every window are complete for this
-// panel set: they are flushed to p_out with FP64 atomics (one per bin per
-// panel set, not per panel) and the window slides.
+// compute warps; warp w owns observers o_begin + w + NW m (m < obs_per_warp)
+// of the group and keeps, per observer, a window of `win` bins in shared
+// memory.  Lanes map to source samples (k = k0 + lane + 32 j, j < TK), so each
+// X row is loaded once per warp and reused for all of the warp's observers,
+// the coefficient record is a warp-uniform broadcast, and the window updates
+// are conflict-free (consecutive lanes, consecutive bins).  The per-(p, o)
+// shift only moves the window offset, never the lane pattern.  After each
+// chunk of 32 TK samples the oldest 32 TK bins of every window are complete
+// for this panel set: they are flushed to p_out with FP64 atomics (one per bin
+// per panel set, not per panel) and the window slides.
+//
+// Two ways to feed the compute warps:
+//  * direct: every warp loads its X rows and coefficient records from global
+//    memory (L1/L2) itself;
+//  * TMA pipeline: one producer warp streams, per (chunk, panel) step, the X
+//    rows (a 2D tensor-map load, 128B swizzled so the per-lane row reads are
+//    bank-conflict-free) and the group's coefficient records (a 1D bulk
+//    copy) into a ring of shared-memory stages; full/empty mbarriers hand the
+//    stages over.  Every wait is bounded by a clock limit: on expiry the
+//    kernel raises kErrTimeout, stops issuing copies, waits (bounded) for the
+//    copies already in flight and leaves.
 //
 // Window bound: a panel set's shifts for one observer span S = i0max - i0min;
-// slots touched in a chunk are [0, CH + S], so S <= win - CH - 1 is required
-// (the host planner bounds S from the set's extent; a violation is flagged,
-// never written out of bounds).
+// slots touched in a chunk are [0, CH + S], so S <= win - CH - 1 is required.
+// The host planner bounds S from the set's extent; the plan kernel records,
+// per (set, observer), i0max and, per (panel, observer) record, the window
+// offset i0max - i0 clamped to [0, win - CH - 1], raising kErrWindow if the
+// bound is exceeded; the hot loop adds that offset and can never leave the
+// window.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "fwh_internal.cuh"
 
 namespace fwh {
@@ -34,6 +51,7 @@ namespace fwh {
 namespace {
 
 constexpr int kMaxObsPerWarp = 16;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 template <typename T> struct Vec;
 template <> struct Vec<float> {
@@ -56,6 +74,12 @@ __device__ __forceinline__ int rec_i0<double>(const double *rec) {
   return (int)__ldg(rec + 12);
 }
 
+template <typename T> __device__ __forceinline__ int rec_i0_of(T v);
+template <> __device__ __forceinline__ int rec_i0_of<float>(float v) {
+  return __float_as_int(v);
+}
+template <> __device__ __forceinline__ int rec_i0_of<double>(double v) { return (int)v; }
+
 template <typename T>
 __device__ __forceinline__ void load16(const T *src, T (&dst)[kRec]) {
   using V = typename Vec<T>::V;
@@ -72,142 +96,246 @@ __device__ __forceinline__ void load16(const T *src, T (&dst)[kRec]) {
   }
 }
 
-template <typename T> __device__ __forceinline__ int rec_i0_of(T v);
-template <> __device__ __forceinline__ int rec_i0_of<float>(float v) {
-  return __float_as_int(v);
+// Shared-memory broadcast read of a 16-value record.
+template <typename T>
+__device__ __forceinline__ void lds16(const T *src, T (&dst)[kRec]) {
+  using V = typename Vec<T>::V;
+  constexpr int per = Vec<T>::per;
+  const V *s = reinterpret_cast<const V *>(src);
+#pragma unroll
+  for (int q = 0; q < kRec / per; ++q) {
+    V v = s[q];
+    if constexpr (per == 4) {
+      dst[4 * q] = v.x; dst[4 * q + 1] = v.y; dst[4 * q + 2] = v.z; dst[4 * q + 3] = v.w;
+    } else {
+      dst[2 * q] = v.x; dst[2 * q + 1] = v.y;
+    }
+  }
 }
-template <> __device__ __forceinline__ int rec_i0_of<double>(double v) { return (int)v; }
 
-__device__ __forceinline__ void atomic_add_f64(double *addr, double v) {
-  atomicAdd(addr, v);
+// One X row from a TMA stage written with SWIZZLE_128B.  The swizzle XORs the
+// 16-byte chunk index (address bits 4..6) with address bits 7..9.  FP64 rows
+// are 128 B, so chunk q of row r sits at chunk q ^ (r & 7) of that row; FP32
+// rows are 64 B, two per 128-byte line, so chunk q of row r is chunk
+// (((r & 1) << 2) | q) ^ ((r >> 1) & 7) of line r >> 1.  Consecutive rows read
+// by 8 consecutive lanes then hit 8 distinct 16-byte bank groups.
+template <typename T>
+__device__ __forceinline__ void lds_row_swz(const unsigned char *stg, int r, T (&dst)[kRec]) {
+  using V = typename Vec<T>::V;
+  constexpr int per = Vec<T>::per;
+#pragma unroll
+  for (int q = 0; q < kRec / per; ++q) {
+    const unsigned char *addr;
+    if constexpr (sizeof(T) == 4) {
+      addr = stg + (size_t)(r >> 1) * 128 + (((((r & 1) << 2) | q) ^ ((r >> 1) & 7)) << 4);
+    } else {
+      addr = stg + (size_t)r * 128 + ((q ^ (r & 7)) << 4);
+    }
+    const V v = *reinterpret_cast<const V *>(addr);
+    if constexpr (per == 4) {
+      dst[4 * q] = v.x; dst[4 * q + 1] = v.y; dst[4 * q + 2] = v.z; dst[4 * q + 3] = v.w;
+    } else {
+      dst[2 * q] = v.x; dst[2 * q + 1] = v.y;
+    }
+  }
 }
 
-// One work item.  smem: NW * obs_per_warp * win values of T; st: int state.
-template <typename T, int TK, int NW>
-__device__ __forceinline__ void process_item(const FwdArgs<T> &a, int item, T *smem,
-                                             int *st) {
-  constexpr int CH = 32 * TK;
-  const int lane = threadIdx.x & 31;
-  const int w = threadIdx.x >> 5;
-  const int ng = a.n_obs_groups;
-  const int g = item % ng;
-  const int rest = item / ng;
-  const int sidx = rest % a.nsets;
-  const int q = rest / a.nsets;
-  const int p_begin = a.set_begin[sidx], p_end = a.set_begin[sidx + 1];
-  const int opw = a.obs_per_cta / NW;
-  const int o_begin = g * a.obs_per_cta;
-  const int o_end = min(a.O, o_begin + a.obs_per_cta);
-  const int k_begin = q * a.seg_len;
-  const int k_end = min(a.ntp, k_begin + a.seg_len);
-  const int win = a.win;
-  T *wwin = smem + (size_t)w * opw * win;
-  int *s_i0max = st + w * kMaxObsPerWarp;
-  int *s_ok = st + NW * kMaxObsPerWarp + w * kMaxObsPerWarp;
+// ---- mbarrier / TMA primitives (PTX) -------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false on timeout (flag raised) or when another warp aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int *err,
+                                          volatile int *abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      atomicOr(err, kErrTimeout);
+      *abort = 1;
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// Warm L2 with a contiguous range ahead of its TMA load (no completion to wait for).
+__device__ __forceinline__ void prefetch_l2(const void *src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes,
+                                          uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
 
-  // observers of this warp
-  int nobs = 0;
-  for (int m = 0; m < opw; ++m)
-    if (o_begin + w + NW * m < o_end) nobs = m + 1;
+__device__ __forceinline__ void atomic_add_f64(double *addr, double v) { atomicAdd(addr, v); }
 
-  // per-observer shift range over the panel set
-  for (int m = 0; m < nobs; ++m) {
-    const int o = o_begin + w + NW * m;
+template <typename T> __device__ __forceinline__ T int_as_rec(int v);
+template <> __device__ __forceinline__ float int_as_rec<float>(int v) { return __int_as_float(v); }
+template <> __device__ __forceinline__ double int_as_rec<double>(int v) { return (double)v; }
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_plan(T *coef, const int *set_begin, int O, int slack,
+                                              int *i0max_tab, int *err) {
+  const int sidx = blockIdx.x;
+  const int pb = set_begin[sidx], pe = set_begin[sidx + 1];
+  for (int o = threadIdx.x; o < O; o += blockDim.x) {
     int lo = 0x7fffffff, hi = -0x7fffffff;
-    for (int p = p_begin + lane; p < p_end; p += 32) {
-      const int i0 = rec_i0<T>(a.coef + ((size_t)p * a.O + o) * kRec);
+    for (int p = pb; p < pe; ++p) {
+      const int i0 = rec_i0_of<T>(coef[((size_t)p * O + o) * kRec + 12]);
       lo = min(lo, i0);
       hi = max(hi, i0);
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
-      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
-    }
-    const bool ok = (hi - lo) <= win - CH - 1;
-    if (lane == 0) {
-      s_i0max[m] = hi;
-      s_ok[m] = ok ? 1 : 0;
-      if (!ok) atomicOr(a.err, kErrWindow);
+    if (hi - lo > slack) atomicOr(err, kErrWindow);
+    i0max_tab[(size_t)sidx * O + o] = hi;
+    for (int p = pb; p < pe; ++p) {
+      T *rec = coef + ((size_t)p * O + o) * kRec;
+      const int off = min(hi - rec_i0_of<T>(rec[12]), slack);
+      rec[13] = int_as_rec<T>(off);
     }
   }
-  for (int i = lane; i < nobs * win; i += 32) wwin[i] = T(0);
+}
+
+// Item decomposition shared by both pipelines.
+template <typename T, int NW>
+struct Item {
+  int sidx, p_begin, p_end, o_begin, o_end, opw, nobs, k_begin, k_end;
+  __device__ __forceinline__ Item(const FwdArgs<T> &a, int item, int w) {
+    const int ng = a.n_obs_groups;
+    const int g = item % ng;
+    const int rest = item / ng;
+    sidx = rest % a.nsets;
+    const int q = rest / a.nsets;
+    p_begin = a.set_begin[sidx];
+    p_end = a.set_begin[sidx + 1];
+    opw = a.obs_per_cta / NW;
+    o_begin = g * a.obs_per_cta;
+    o_end = min(a.O, o_begin + a.obs_per_cta);
+    k_begin = q * a.seg_len;
+    k_end = min(a.ntp, k_begin + a.seg_len);
+    nobs = 0;
+    for (int m = 0; m < opw; ++m)
+      if (o_begin + w + NW * m < o_end) nobs = m + 1;
+  }
+};
+
+// Per-observer largest shift of the panel set (from the plan); zero windows.
+template <typename T, int NW>
+__device__ __forceinline__ void item_prologue(const FwdArgs<T> &a, const Item<T, NW> &it,
+                                              int w, T *wwin, int *s_i0max) {
+  const int lane = threadIdx.x & 31;
+  if (lane < it.nobs)
+    s_i0max[lane] = a.i0max_tab[(size_t)it.sidx * a.O + it.o_begin + w + NW * lane];
+  for (int i = lane; i < it.nobs * a.win; i += 32) wwin[i] = T(0);
   __syncwarp();
+}
 
-  for (int k0 = k_begin; k0 < k_end; k0 += CH) {
-    for (int p = p_begin; p < p_end; ++p) {
-      // observer-independent rows of this panel for the chunk
-      T x[TK][kRec];
-      const T *Xp = a.X + ((size_t)p * a.ntp + k0 + lane) * kRec;
+// Signal, moment and the two spline-node updates of one (panel, observer),
+// one sample per lane per block: read-modify-write of the window; the two
+// node updates of neighbouring lanes meet in one bin, so they are separated
+// by __syncwarp.
+template <typename T, int TK>
+__device__ __forceinline__ void accumulate(const T (&x)[TK][kRec], const T (&c)[kRec], T *wm) {
+  T gv[TK], mv[TK];
 #pragma unroll
-      for (int j = 0; j < TK; ++j) load16<T>(Xp + (size_t)j * 32 * kRec, x[j]);
-
-      const T *rec0 = a.coef + (size_t)p * a.O * kRec;
-      for (int m = 0; m < nobs; ++m) {
-        const int o = o_begin + w + NW * m;
-        T c[kRec];
-        load16<T>(rec0 + (size_t)o * kRec, c);
-        const int i0 = rec_i0_of<T>(c[12]);
-        if (!s_ok[m]) continue;  // warp-uniform
-        // slot of bin (k - i0) relative to the window start
-        // (win start = k0 - i0max - 1 for this chunk)
-        const int slot = k0 + lane - i0 - (k0 - s_i0max[m] - 1);
-        T *wm = wwin + (size_t)m * win + slot;
-        T gv[TK], mv[TK];
+  for (int j = 0; j < TK; ++j) {
+    T g0 = c[0] * x[j][0], m0 = c[0] * x[j][8];
 #pragma unroll
-        for (int j = 0; j < TK; ++j) {
-          T g0 = c[0] * x[j][0], m0 = c[0] * x[j][8];
-#pragma unroll
-          for (int s = 1; s < 8; ++s) {
-            g0 = fma(c[s], x[j][s], g0);
-            m0 = fma(c[s], x[j][8 + s], m0);
-          }
-          gv[j] = g0;
-          mv[j] = m0;
-        }
-#pragma unroll
-        for (int j = 0; j < TK; ++j) {
-          T v = wm[32 * j];
-          v = fma(c[8], gv[j], v);
-          v = fma(c[10], mv[j], v);
-          wm[32 * j] = v;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < TK; ++j) {
-          T v = wm[32 * j - 1];
-          v = fma(c[9], gv[j], v);
-          v = fma(c[11], mv[j], v);
-          wm[32 * j - 1] = v;
-        }
-        __syncwarp();
-      }
+    for (int s = 1; s < 8; ++s) {
+      g0 = fma(c[s], x[j][s], g0);
+      m0 = fma(c[s], x[j][8 + s], m0);
     }
-    // the first CH bins of every window are complete: flush and slide
-    for (int m = 0; m < nobs; ++m) {
-      const int o = o_begin + w + NW * m;
-      T *wm = wwin + (size_t)m * win;
-      const int wbase = k0 - s_i0max[m] - 1;
-      const int nvalid = a.n_valid[o];
-      double *po = a.p_out + (size_t)o * a.nt;
-      for (int t = lane; t < CH; t += 32) {
-        const int bin = wbase + t;
-        const T v = wm[t];
-        if (bin >= 0 && bin < nvalid && v != T(0)) atomic_add_f64(po + bin, (double)v);
-      }
-      __syncwarp();
-      // move live bins [CH, win) to the front (win - CH <= CH), zero the rest
-      for (int t = lane; t < win - CH; t += 32) wm[t] = wm[CH + t];
-      __syncwarp();
-      for (int t = win - CH + lane; t < win; t += 32) wm[t] = T(0);
-      __syncwarp();
-    }
+    gv[j] = g0;
+    mv[j] = m0;
   }
-  // segment end: the remaining window holds partial bins of the next chunk
-  for (int m = 0; m < nobs; ++m) {
-    const int o = o_begin + w + NW * m;
+#pragma unroll
+  for (int j = 0; j < TK; ++j) {
+    T v = wm[32 * j];
+    v = fma(c[8], gv[j], v);
+    v = fma(c[10], mv[j], v);
+    wm[32 * j] = v;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < TK; ++j) {
+    T v = wm[32 * j - 1];
+    v = fma(c[9], gv[j], v);
+    v = fma(c[11], mv[j], v);
+    wm[32 * j - 1] = v;
+  }
+  __syncwarp();
+}
+
+// Flush the first CH (complete) bins of every window to p_out and slide.
+template <typename T, int CH, int NW>
+__device__ __forceinline__ void flush_slide(const FwdArgs<T> &a, const Item<T, NW> &it, int w,
+                                            T *wwin, const int *s_i0max, int k0) {
+  const int lane = threadIdx.x & 31;
+  const int win = a.win;
+  for (int m = 0; m < it.nobs; ++m) {
+    const int o = it.o_begin + w + NW * m;
     T *wm = wwin + (size_t)m * win;
-    const int wbase = k_end - s_i0max[m] - 1;
+    const int wbase = k0 - s_i0max[m] - 1;
+    const int nvalid = a.n_valid[o];
+    double *po = a.p_out + (size_t)o * a.nt;
+    for (int t = lane; t < CH; t += 32) {
+      const int bin = wbase + t;
+      const T v = wm[t];
+      if (bin >= 0 && bin < nvalid && v != T(0)) atomic_add_f64(po + bin, (double)v);
+    }
+    __syncwarp();
+    for (int t = lane; t < win - CH; t += 32) wm[t] = wm[CH + t];  // win - CH <= CH
+    __syncwarp();
+    for (int t = win - CH + lane; t < win; t += 32) wm[t] = T(0);
+    __syncwarp();
+  }
+}
+
+// Segment end: the remaining window holds partial bins of the next segment.
+template <typename T, int CH, int NW>
+__device__ __forceinline__ void flush_tail(const FwdArgs<T> &a, const Item<T, NW> &it, int w,
+                                           T *wwin, const int *s_i0max) {
+  const int lane = threadIdx.x & 31;
+  const int win = a.win;
+  for (int m = 0; m < it.nobs; ++m) {
+    const int o = it.o_begin + w + NW * m;
+    T *wm = wwin + (size_t)m * win;
+    const int wbase = it.k_end - s_i0max[m] - 1;
     const int nvalid = a.n_valid[o];
     double *po = a.p_out + (size_t)o * a.nt;
     for (int t = lane; t < win - CH; t += 32) {
@@ -219,22 +347,380 @@ __device__ __forceinline__ void process_item(const FwdArgs<T> &a, int item, T *s
   __syncwarp();
 }
 
+// ---- direct-load pipeline --------------------------------------------------
 template <typename T, int TK, int NW>
-__global__ void __launch_bounds__(NW * 32) k_forward(FwdArgs<T> a) {
+__device__ __forceinline__ void process_item_direct(const FwdArgs<T> &a, int item, T *smem,
+                                                    int *st) {
+  constexpr int CH = 32 * TK;
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const Item<T, NW> it(a, item, w);
+  T *wwin = smem + (size_t)w * it.opw * a.win;
+  int *s_i0max = st + w * kMaxObsPerWarp;
+  item_prologue<T, NW>(a, it, w, wwin, s_i0max);
+  for (int k0 = it.k_begin; k0 < it.k_end; k0 += CH) {
+    for (int p = it.p_begin; p < it.p_end; ++p) {
+      T x[TK][kRec];
+      const T *Xp = a.X + ((size_t)p * a.ntp + k0 + lane) * kRec;
+#pragma unroll
+      for (int j = 0; j < TK; ++j) load16<T>(Xp + (size_t)j * 32 * kRec, x[j]);
+      const T *rec0 = a.coef + (size_t)p * a.O * kRec;
+      for (int m = 0; m < it.nobs; ++m) {
+        const int o = it.o_begin + w + NW * m;
+        T c[kRec];
+        load16<T>(rec0 + (size_t)o * kRec, c);
+        T *wm = wwin + (m * a.win + 1 + lane + rec_i0_of<T>(c[13]));
+        accumulate<T, TK>(x, c, wm);
+      }
+    }
+    flush_slide<T, CH, NW>(a, it, w, wwin, s_i0max, k0);
+  }
+  flush_tail<T, CH, NW>(a, it, w, wwin, s_i0max);
+}
+
+// ---- TMA pipeline ------------------------------------------------------------
+struct PipeState {
+  uint64_t *full, *empty;
+  unsigned char *stage0;
+  unsigned stage_bytes, x_bytes;
+  int nst;
+  volatile int *abort;
+};
+
+// Producer (one lane): stream the steps of one item into the stage ring, and
+// warm L2 with the rows and records kPrefetchSteps steps beyond the ring so
+// that the stage loads hit L2 instead of waiting for HBM.
+constexpr int kPrefetchSteps = 8;
+
+template <typename T, int TK, int NW>
+__device__ __forceinline__ void produce_item(const FwdArgs<T> &a, const Item<T, 1> &it,
+                                             const PipeState &ps, unsigned &step) {
+  constexpr int CH = 32 * TK;
+  const unsigned cbytes = (unsigned)((it.o_end - it.o_begin) * kRec * sizeof(T));
+  const int np = it.p_end - it.p_begin;
+  const int nsteps = np * ((it.k_end - it.k_begin) / CH);
+  auto src_x = [&](int idx) {
+    const int p = it.p_begin + idx % np;
+    const int k0 = it.k_begin + (idx / np) * CH;
+    return a.X + ((size_t)p * a.ntp + k0) * kRec;
+  };
+  auto src_c = [&](int idx) {
+    const int p = it.p_begin + idx % np;
+    return a.coef + ((size_t)p * a.O + it.o_begin) * kRec;
+  };
+  for (int idx = 0; idx < min(nsteps, ps.nst + kPrefetchSteps); ++idx) {
+    prefetch_l2(src_x(idx), ps.x_bytes);
+    prefetch_l2(src_c(idx), cbytes);
+  }
+  for (int idx = 0; idx < nsteps; ++idx, ++step) {
+    if (*ps.abort) return;
+    const int pf = idx + ps.nst + kPrefetchSteps;
+    if (pf < nsteps) {
+      prefetch_l2(src_x(pf), ps.x_bytes);
+      prefetch_l2(src_c(pf), cbytes);
+    }
+    const int p = it.p_begin + idx % np;
+    const int k0 = it.k_begin + (idx / np) * CH;
+    const int s = (int)(step % (unsigned)ps.nst);
+    const unsigned ph = (step / (unsigned)ps.nst) & 1u;
+    if (step >= (unsigned)ps.nst && !mbar_wait(&ps.empty[s], ph ^ 1u, a.err, ps.abort)) return;
+    unsigned char *dst = ps.stage0 + (size_t)s * ps.stage_bytes;
+    mbar_expect_tx(&ps.full[s], ps.x_bytes + cbytes);
+    // tensor rows are 128 bytes: two FP32 samples or one FP64 sample
+    tma_load_2d(dst, a.tmX, 0, (p * a.ntp + k0) / (sizeof(T) == 4 ? 2 : 1), &ps.full[s]);
+    bulk_load(dst + ps.x_bytes, src_c(idx), cbytes, &ps.full[s]);
+  }
+}
+
+template <typename T, int TK, int NW>
+__device__ __forceinline__ void consume_item(const FwdArgs<T> &a, const Item<T, NW> &it,
+                                             const PipeState &ps, unsigned &step, T *wwin,
+                                             int *s_i0max) {
+  constexpr int CH = 32 * TK;
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  item_prologue<T, NW>(a, it, w, wwin, s_i0max);
+  for (int k0 = it.k_begin; k0 < it.k_end; k0 += CH) {
+    for (int p = it.p_begin; p < it.p_end; ++p, ++step) {
+      const int s = (int)(step % (unsigned)ps.nst);
+      const unsigned ph = (step / (unsigned)ps.nst) & 1u;
+      if (!mbar_wait(&ps.full[s], ph, a.err, ps.abort)) return;
+      const unsigned char *stg = ps.stage0 + (size_t)s * ps.stage_bytes;
+      T x[TK][kRec];
+#pragma unroll
+      for (int j = 0; j < TK; ++j) lds_row_swz<T>(stg, lane + 32 * j, x[j]);
+      const T *crec = reinterpret_cast<const T *>(stg + ps.x_bytes);
+      for (int m = 0; m < it.nobs; ++m) {
+        const int o = it.o_begin + w + NW * m;
+        T c[kRec];
+        lds16<T>(crec + (size_t)(o - it.o_begin) * kRec, c);
+        T *wm = wwin + (m * a.win + 1 + lane + rec_i0_of<T>(c[13]));
+        accumulate<T, TK>(x, c, wm);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ps.empty[s]);
+    }
+    flush_slide<T, CH, NW>(a, it, w, wwin, s_i0max, k0);
+  }
+  flush_tail<T, CH, NW>(a, it, w, wwin, s_i0max);
+}
+
+// ---- packed FP32x2 consumer (mixed precision) --------------------------------
+// FP32 X rows hold sample pairs interleaved ([k/2][value][k&1]), so the
+// 16-byte chunk c of pair row pi is the two packed operands
+// (x_{2pi}[2c], x_{2pi+1}[2c]) and (x_{2pi}[2c+1], x_{2pi+1}[2c+1]).  Lane l
+// owns pair rows pi = l + 32 t (samples k = k0 + 2 pi and k + 1) and computes
+// both samples' signal and moment with fma.rn.f32x2 (two FMAs per issued
+// instruction):  G = (g_k, g_k+1) = sum_q c_q X[q],  M likewise on the
+// moments, U = a G + cc M (left-node parts), V = b G + dd M (right-node
+// parts).  The bins are B0 = k - i0 - 1 (v_k), B1 = k - i0 (u_k + v_k+1) and
+// B2 = k - i0 + 1 (u_k+1); B0 of lane l is B2 of lane l - 1.  The slot
+// parity of B1 depends only on i0, so each lane updates one aligned pair with
+// a packed 64-bit read-modify-write:
+//  * B1 even: (B1, B2) += (u_k + v_k+1, u_k+1 + v_k+2 of lane l + 1); the bin
+//    below the chunk gets v_k of lane 0, block 0 separately;
+//  * B1 odd:  (B0, B1) += (v_k + u_k-1 of lane l - 1, u_k + v_k+1); the bin
+//    above the chunk gets u of lane 31, last block separately.
+// Within one (panel, observer) no two lanes touch the same bin; one
+// __syncwarp per panel orders the next panel's shifted updates.
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pk2(float lo, float hi) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(u64 r, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ u64 fmul2(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 fadd2(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// Pair row pi of a SWIZZLE_128B stage (128-byte rows): chunk c at c ^ (pi & 7).
+__device__ __forceinline__ void lds_pair_row(const unsigned char *stg, int pi, u64 (&X)[kRec]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const ulonglong2 v =
+        *reinterpret_cast<const ulonglong2 *>(stg + (size_t)pi * 128 + ((c ^ (pi & 7)) << 4));
+    X[2 * c] = v.x;
+    X[2 * c + 1] = v.y;
+  }
+}
+
+template <int TK, int NW>
+__device__ __forceinline__ void consume_item_f32x2(const FwdArgs<float> &a,
+                                                   const Item<float, NW> &it,
+                                                   const PipeState &ps, unsigned &step,
+                                                   float *wwin, int *s_i0max) {
+  constexpr int CH = 32 * TK;
+  constexpr int NP = TK / 2;  // pair rows per lane
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  item_prologue<float, NW>(a, it, w, wwin, s_i0max);
+  for (int k0 = it.k_begin; k0 < it.k_end; k0 += CH) {
+    for (int p = it.p_begin; p < it.p_end; ++p, ++step) {
+      const int s = (int)(step % (unsigned)ps.nst);
+      const unsigned ph = (step / (unsigned)ps.nst) & 1u;
+      if (!mbar_wait(&ps.full[s], ph, a.err, ps.abort)) return;
+      const unsigned char *stg = ps.stage0 + (size_t)s * ps.stage_bytes;
+      u64 X[NP][kRec];
+#pragma unroll
+      for (int t = 0; t < NP; ++t) lds_pair_row(stg, lane + 32 * t, X[t]);
+      const float *crec = reinterpret_cast<const float *>(stg + ps.x_bytes) + (size_t)w * kRec;
+      float c[kRec];
+      if (it.nobs > 0) lds16<float>(crec, c);
+      for (int m = 0; m < it.nobs; ++m) {
+        float *w1 = wwin + (m * a.win + 1 + 2 * lane + rec_i0_of<float>(c[13]));
+        const bool even = ((reinterpret_cast<uintptr_t>(w1) >> 2) & 1) == 0;
+        float *w64 = even ? w1 : w1 - 1;
+        u64 old[NP];
+#pragma unroll
+        for (int t = 0; t < NP; ++t) old[t] = *reinterpret_cast<const u64 *>(w64 + 64 * t);
+        float cn[kRec];
+        if (m + 1 < it.nobs) lds16<float>(crec + (size_t)(m + 1) * NW * kRec, cn);
+        u64 U[NP], V[NP];
+#pragma unroll
+        for (int t = 0; t < NP; ++t) {
+          u64 G = fmul2(pk2(c[0], c[0]), X[t][0]);
+          u64 M = fmul2(pk2(c[0], c[0]), X[t][8]);
+#pragma unroll
+          for (int q = 1; q < 8; ++q) {
+            const u64 cq = pk2(c[q], c[q]);
+            G = ffma2(cq, X[t][q], G);
+            M = ffma2(cq, X[t][8 + q], M);
+          }
+          U[t] = ffma2(pk2(c[10], c[10]), M, fmul2(pk2(c[8], c[8]), G));
+          V[t] = ffma2(pk2(c[11], c[11]), M, fmul2(pk2(c[9], c[9]), G));
+        }
+        if (even) {
+          float va[NP], vb[NP], sv[NP];
+#pragma unroll
+          for (int t = 0; t < NP; ++t) {
+            upk2(V[t], va[t], vb[t]);
+            sv[t] = __shfl_sync(0xffffffffu, va[t], (lane + 1) & 31);
+          }
+#pragma unroll
+          for (int t = 0; t < NP; ++t) {
+            // lane 31's B2 is lane 0's B0 of the next block (none after the last)
+            const float ex = lane < 31 ? sv[t] : (t + 1 < NP ? sv[t + 1 < NP ? t + 1 : t] : 0.f);
+            const u64 wv = fadd2(U[t], pk2(vb[t], ex));
+            *reinterpret_cast<u64 *>(w64 + 64 * t) = fadd2(old[t], wv);
+          }
+          if (lane == 0) w1[-1] += va[0];  // bin below the chunk
+        } else {
+          float ua[NP], ub[NP], va[NP], vb[NP], su[NP];
+#pragma unroll
+          for (int t = 0; t < NP; ++t) {
+            upk2(U[t], ua[t], ub[t]);
+            upk2(V[t], va[t], vb[t]);
+            su[t] = __shfl_sync(0xffffffffu, ub[t], (lane + 31) & 31);
+          }
+#pragma unroll
+          for (int t = 0; t < NP; ++t) {
+            // lane 0's B0 is lane 31's B2 of the previous block (none before the first)
+            const float ex = lane > 0 ? su[t] : (t > 0 ? su[t > 0 ? t - 1 : t] : 0.f);
+            const u64 wv = fadd2(pk2(va[t], ua[t]), pk2(ex, vb[t]));
+            *reinterpret_cast<u64 *>(w64 + 64 * t) = fadd2(old[t], wv);
+          }
+          if (lane == 31) w1[64 * (NP - 1) + 1] += ub[NP - 1];  // bin above the chunk
+        }
+        if (m + 1 < it.nobs) {
+#pragma unroll
+          for (int q = 0; q < kRec; ++q) c[q] = cn[q];
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ps.empty[s]);
+    }
+    flush_slide<float, CH, NW>(a, it, w, wwin, s_i0max, k0);
+  }
+  flush_tail<float, CH, NW>(a, it, w, wwin, s_i0max);
+}
+
+// Wait (bounded) until every copy the producer issued has landed.
+__device__ __forceinline__ void drain_copies(const PipeState &ps, unsigned step, int *err) {
+  const unsigned first = step > (unsigned)ps.nst ? step - (unsigned)ps.nst : 0u;
+  volatile int never = 0;
+  for (unsigned t = first; t < step; ++t) {
+    const int s = (int)(t % (unsigned)ps.nst);
+    mbar_wait(&ps.full[s], (t / (unsigned)ps.nst) & 1u, err, &never);
+  }
+}
+
+template <typename T, int TK, int NW>
+__device__ __forceinline__ unsigned char *pipe_setup(unsigned char *raw, int obs_per_cta,
+                                                     int nst, uint64_t *bars,
+                                                     volatile int *abort, PipeState &ps) {
+  constexpr int CH = 32 * TK;
+  const unsigned base = smem_u32(raw);
+  unsigned char *al = raw + ((1024u - (base & 1023u)) & 1023u);
+  ps.x_bytes = CH * kRec * sizeof(T);
+  ps.stage_bytes = (ps.x_bytes + obs_per_cta * kRec * sizeof(T) + 1023u) & ~1023u;
+  ps.nst = nst;
+  ps.stage0 = al;
+  ps.full = bars;
+  ps.empty = bars + nst;
+  ps.abort = abort;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nst; ++s) {
+      mbar_init(&ps.full[s], 1);
+      mbar_init(&ps.empty[s], NW);
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  return al + (size_t)nst * ps.stage_bytes;  // windows follow the stages
+}
+
+constexpr int kMaxStages = 8;
+
+// CTAs per SM the register budget is sized for: TMA shapes with 4 compute
+// warps run 3 (TK = 4) or 2 (TK = 8) per SM, with 8 compute warps 2 or 1.
+template <int TK, int NW, int PIPE>
+struct MinBlocks {
+  static constexpr int v = !PIPE ? 1 : (NW <= 4 ? (TK <= 4 ? 3 : 2) : (TK <= 4 ? 2 : 1));
+};
+
+template <typename T, int TK, int NW, int PIPE, int ACC>
+__device__ __forceinline__ void forward_cta(const FwdArgs<T> &a, int nst) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int st[2 * NW * kMaxObsPerWarp];
-  process_item<T, TK, NW>(a, blockIdx.x, reinterpret_cast<T *>(smem_raw), st);
+  __shared__ int st[NW * kMaxObsPerWarp];
+  if constexpr (PIPE == 0) {
+    process_item_direct<T, TK, NW>(a, blockIdx.x, reinterpret_cast<T *>(smem_raw), st);
+  } else {
+    __shared__ __align__(8) uint64_t bars[2 * kMaxStages];
+    __shared__ int abort_flag;
+    PipeState ps;
+    unsigned char *wbase = pipe_setup<T, TK, NW>(smem_raw, a.obs_per_cta, nst, bars,
+                                                 &abort_flag, ps);
+    const int w = threadIdx.x >> 5;
+    unsigned step = 0;
+    if (w == NW) {
+      if ((threadIdx.x & 31) == 0) {
+        const Item<T, 1> it(a, blockIdx.x, 0);
+        produce_item<T, TK, NW>(a, it, ps, step);
+        drain_copies(ps, step, a.err);
+      }
+    } else {
+      const Item<T, NW> it(a, blockIdx.x, w);
+      T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.win;
+      if constexpr (ACC == 3 && sizeof(T) == 4) {
+        consume_item_f32x2<TK, NW>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
+      } else {
+        consume_item<T, TK, NW>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
+      }
+    }
+  }
+}
+
+
+template <typename T, int TK, int NW, int PIPE, int ACC>
+__global__ void __launch_bounds__((NW + PIPE) * 32, (MinBlocks<TK, NW, PIPE>::v))
+    k_forward(FwdArgs<T> a, int nst) {
+  forward_cta<T, TK, NW, PIPE, ACC>(a, nst);
+}
+
+// Same CTA program for the long-sample-block shapes (TK = 8), which need
+// about 190 registers: capped at 200 so that two CTAs still share an SM.
+template <typename T, int TK, int NW, int PIPE, int ACC>
+__global__ void __maxnreg__(200) k_forward_wide(FwdArgs<T> a, int nst) {
+  forward_cta<T, TK, NW, PIPE, ACC>(a, nst);
 }
 
 // Persistent form: CTAs pull work items of several surfaces from one queue.
-template <typename T, int TK, int NW>
-__global__ void __launch_bounds__(NW * 32) k_forward_batch(const FwdArgs<T> *args,
-                                                           const int *item_prefix,
-                                                           int n_surf, int total,
-                                                           int *counter) {
+template <typename T, int TK, int NW, int PIPE, int ACC>
+__global__ void __launch_bounds__((NW + PIPE) * 32, (MinBlocks<TK, NW, PIPE>::v)) k_forward_batch(
+    const FwdArgs<T> *args,
+                                                                     const int *item_prefix,
+                                                                     int n_surf, int total,
+                                                                     int *counter, int nst) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int st[2 * NW * kMaxObsPerWarp];
+  __shared__ int st[NW * kMaxObsPerWarp];
   __shared__ int s_item;
+  __shared__ __align__(8) uint64_t bars[2 * kMaxStages];
+  __shared__ int abort_flag;
+  PipeState ps;
+  unsigned char *wbase = smem_raw;
+  if constexpr (PIPE == 1) {
+    int maxo = 0;
+    for (int i = 0; i < n_surf; ++i) maxo = max(maxo, args[i].obs_per_cta);
+    wbase = pipe_setup<T, TK, NW>(smem_raw, maxo, nst, bars, &abort_flag, ps);
+  }
+  const int w = threadIdx.x >> 5;
+  unsigned step = 0;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
@@ -247,45 +733,81 @@ __global__ void __launch_bounds__(NW * 32) k_forward_batch(const FwdArgs<T> *arg
       if (item_prefix[mid] <= item) lo = mid; else hi = mid - 1;
     }
     const FwdArgs<T> a = args[lo];
-    process_item<T, TK, NW>(a, item - item_prefix[lo], reinterpret_cast<T *>(smem_raw), st);
+    const int li = item - item_prefix[lo];
+    if constexpr (PIPE == 0) {
+      process_item_direct<T, TK, NW>(a, li, reinterpret_cast<T *>(smem_raw), st);
+    } else {
+      if (abort_flag) break;
+      if (w == NW) {
+        if ((threadIdx.x & 31) == 0) {
+          const Item<T, 1> it(a, li, 0);
+          produce_item<T, TK, NW>(a, it, ps, step);
+        }
+      } else {
+        const Item<T, NW> it(a, li, w);
+        T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.win;
+        if constexpr (ACC == 3 && sizeof(T) == 4) {
+          consume_item_f32x2<TK, NW>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
+        } else {
+          consume_item<T, TK, NW>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
+        }
+      }
+    }
+  }
+  if constexpr (PIPE == 1) {
+    if (w == NW && (threadIdx.x & 31) == 0) drain_copies(ps, step, args[0].err);
   }
 }
 
-// Candidate tile shapes: {tk, warps, obs_per_warp (max), win, seg_chunks}.
+// Candidate tile shapes {pipe, tk, warps, obs_per_warp, win, seg_chunks, stages}.
+// acc: 0 one sample per lane per block (FP64), 3 packed FP32x2 sample pairs
+// (FP32; the FP32 series layout is pair-interleaved, so every FP32 shape is a
+// TMA shape).
 const FwdConfig kCfgF32[] = {
-    {4, 8, 16, 256, 4},
-    {4, 4, 16, 256, 4},
-    {2, 8, 16, 128, 8},
-    {4, 8, 16, 256, 2},
-    {4, 8, 16, 256, 8},
+    {1, 4, 4, 9, 224, 4, 3, 3, 0},
+    {1, 4, 4, 9, 224, 4, 6, 3, 1},
+    {1, 4, 8, 9, 224, 4, 4, 3, 1},
+    {1, 8, 4, 9, 352, 2, 4, 3, 1},
 };
 const FwdConfig kCfgF64[] = {
-    {2, 8, 16, 128, 8},
-    {2, 4, 16, 128, 8},
-    {1, 8, 16, 64, 16},
+    {0, 2, 8, 16, 128, 8, 0, 0, 0},
+    {1, 2, 8, 9, 128, 8, 3, 0, 0},
+    {0, 2, 4, 16, 128, 8, 0, 0, 0},
+    {0, 1, 8, 16, 64, 16, 0, 0, 0},
 };
 
-template <typename T, int TK, int NW>
-cudaError_t launch_tk_nw(const FwdArgs<T> &a, const FwdConfig &c, cudaStream_t s) {
-  const size_t smem = (size_t)NW * (a.obs_per_cta / NW) * a.win * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(k_forward<T, TK, NW>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename T>
+size_t smem_for(const FwdConfig &c, int obs_per_cta) {
+  const int opw = obs_per_cta / c.warps;
+  size_t win = (size_t)c.warps * opw * c.win * sizeof(T);
+  if (c.pipe == 0) return win;
+  const size_t xb = (size_t)32 * c.tk * kRec * sizeof(T);
+  const size_t sb = (xb + (size_t)obs_per_cta * kRec * sizeof(T) + 1023) & ~size_t(1023);
+  return 1024 + (size_t)c.stages * sb + win;
+}
+
+template <typename T, int TK, int NW, int PIPE, int ACC>
+cudaError_t launch_one(const FwdArgs<T> &a, const FwdConfig &c, cudaStream_t s) {
+  const size_t smem = smem_for<T>(c, a.obs_per_cta);
+  auto kern = c.wide ? k_forward_wide<T, TK, NW, PIPE, ACC> : k_forward<T, TK, NW, PIPE, ACC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   const int items = a.nsets * a.n_obs_groups * a.n_segs;
   if (items <= 0) return cudaSuccess;
-  k_forward<T, TK, NW><<<items, NW * 32, smem, s>>>(a);
+  kern<<<items, (NW + PIPE) * 32, smem, s>>>(a, c.stages);
   return cudaGetLastError();
 }
 
-template <typename T, int TK, int NW>
-cudaError_t launch_batch_tk_nw(const FwdArgs<T> *d_args, const int *d_prefix, int n_surf,
-                               int total, int *d_counter, size_t smem, int n_ctas,
-                               cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_forward_batch<T, TK, NW>,
+template <typename T, int TK, int NW, int PIPE, int ACC>
+cudaError_t launch_batch_one(const FwdArgs<T> *d_args, const int *d_prefix, int n_surf,
+                             int total, int *d_counter, size_t smem, int n_ctas, int nst,
+                             cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_forward_batch<T, TK, NW, PIPE, ACC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_forward_batch<T, TK, NW><<<n_ctas, NW * 32, smem, s>>>(d_args, d_prefix, n_surf, total,
-                                                          d_counter);
+  k_forward_batch<T, TK, NW, PIPE, ACC><<<n_ctas, (NW + PIPE) * 32, smem, s>>>(
+      d_args, d_prefix, n_surf, total, d_counter, nst);
   return cudaGetLastError();
 }
 
@@ -302,63 +824,93 @@ FwdConfig fwd_config(bool fp64, int idx) {
   return fp64 ? kCfgF64[idx] : kCfgF32[idx];
 }
 
-template <>
-cudaError_t launch_forward<float>(const FwdArgs<float> &a, int cfg, cudaStream_t s) {
-  const FwdConfig c = fwd_config(false, cfg);
-  if (c.tk == 4 && c.warps == 8) return launch_tk_nw<float, 4, 8>(a, c, s);
-  if (c.tk == 4 && c.warps == 4) return launch_tk_nw<float, 4, 4>(a, c, s);
-  if (c.tk == 2 && c.warps == 8) return launch_tk_nw<float, 2, 8>(a, c, s);
-  return cudaErrorInvalidValue;
+size_t fwd_smem_bytes(bool fp64, const FwdConfig &c, int obs_per_cta) {
+  return fp64 ? smem_for<double>(c, obs_per_cta) : smem_for<float>(c, obs_per_cta);
 }
 
-template <>
-cudaError_t launch_forward<double>(const FwdArgs<double> &a, int cfg, cudaStream_t s) {
-  const FwdConfig c = fwd_config(true, cfg);
-  if (c.tk == 2 && c.warps == 8) return launch_tk_nw<double, 2, 8>(a, c, s);
-  if (c.tk == 2 && c.warps == 4) return launch_tk_nw<double, 2, 4>(a, c, s);
-  if (c.tk == 1 && c.warps == 8) return launch_tk_nw<double, 1, 8>(a, c, s);
-  return cudaErrorInvalidValue;
+bool encode_x_tensor_map(void *out128, const void *X, unsigned long long rows, bool fp64,
+                         int box_rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  // Rows of 128 bytes (two FP32 samples or one FP64 sample of 16 values), so
+  // the inner box dimension equals the 128-byte swizzle span.
+  const unsigned per = fp64 ? 1u : 2u;  // samples per 128-byte row
+  const cuuint64_t dims[2] = {fp64 ? 16ull : 32ull, rows / per};
+  const cuuint64_t strides[1] = {128ull};
+  const cuuint32_t box[2] = {fp64 ? 16u : 32u, (cuuint32_t)(box_rows / per)};
+  const cuuint32_t estr[2] = {1, 1};
+  CUtensorMap *m = reinterpret_cast<CUtensorMap *>(out128);
+  const CUresult r = enc(m, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                         2, const_cast<void *>(X), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Instantiated shapes: FP32 {TMA packed 4x8, 4x4, 8x4}; FP64 {direct 2x8,
+// TMA 2x8, direct 2x4, direct 1x8}.
+#define FWH_DISPATCH(T, c, CALL)                                                        \
+  do {                                                                                   \
+    if constexpr (sizeof(T) == 4) {                                                      \
+      if (c.pipe == 1 && c.tk == 4 && c.warps == 8 && c.acc == 3) return CALL(T, 4, 8, 1, 3); \
+      if (c.pipe == 1 && c.tk == 4 && c.warps == 4 && c.acc == 3) return CALL(T, 4, 4, 1, 3); \
+      if (c.pipe == 1 && c.tk == 8 && c.warps == 4 && c.acc == 3) return CALL(T, 8, 4, 1, 3); \
+    } else {                                                                             \
+      if (c.pipe == 0 && c.tk == 2 && c.warps == 8) return CALL(T, 2, 8, 0, 0);          \
+      if (c.pipe == 1 && c.tk == 2 && c.warps == 8) return CALL(T, 2, 8, 1, 0);          \
+      if (c.pipe == 0 && c.tk == 2 && c.warps == 4) return CALL(T, 2, 4, 0, 0);          \
+      if (c.pipe == 0 && c.tk == 1 && c.warps == 8) return CALL(T, 1, 8, 0, 0);          \
+    }                                                                                    \
+    return cudaErrorInvalidValue;                                                        \
+  } while (0)
+
+template <typename T>
+cudaError_t launch_forward(const FwdArgs<T> &a, int cfg, cudaStream_t s) {
+  const FwdConfig c = fwd_config(sizeof(T) == 8, cfg);
+#define FWH_CALL_ONE(TT, TK, NW, PIPE, ACC) launch_one<TT, TK, NW, PIPE, ACC>(a, c, s)
+  FWH_DISPATCH(T, c, FWH_CALL_ONE);
+#undef FWH_CALL_ONE
 }
 
 template <typename T>
 cudaError_t launch_forward_batch(const FwdArgs<T> *d_args, const int *d_prefix, int n_surf,
                                  int total, int *d_counter, int cfg, int n_ctas,
-                                 cudaStream_t s);
-
-template <>
-cudaError_t launch_forward_batch<float>(const FwdArgs<float> *d_args, const int *d_prefix,
-                                        int n_surf, int total, int *d_counter, int cfg,
-                                        int n_ctas, cudaStream_t s) {
-  const FwdConfig c = fwd_config(false, cfg);
-  const size_t smem = (size_t)c.warps * c.obs_per_warp * c.win * sizeof(float);
-  if (c.tk == 4 && c.warps == 8)
-    return launch_batch_tk_nw<float, 4, 8>(d_args, d_prefix, n_surf, total, d_counter, smem,
-                                           n_ctas, s);
-  if (c.tk == 4 && c.warps == 4)
-    return launch_batch_tk_nw<float, 4, 4>(d_args, d_prefix, n_surf, total, d_counter, smem,
-                                           n_ctas, s);
-  if (c.tk == 2 && c.warps == 8)
-    return launch_batch_tk_nw<float, 2, 8>(d_args, d_prefix, n_surf, total, d_counter, smem,
-                                           n_ctas, s);
-  return cudaErrorInvalidValue;
+                                 cudaStream_t s) {
+  const FwdConfig c = fwd_config(sizeof(T) == 8, cfg);
+  const size_t smem = smem_for<T>(c, c.warps * c.obs_per_warp);
+#define FWH_CALL_BATCH(TT, TK, NW, PIPE, ACC)                                          \
+  launch_batch_one<TT, TK, NW, PIPE, ACC>(d_args, d_prefix, n_surf, total, d_counter, smem, \
+                                          n_ctas, c.stages, s)
+  FWH_DISPATCH(T, c, FWH_CALL_BATCH);
+#undef FWH_CALL_BATCH
 }
 
-template <>
-cudaError_t launch_forward_batch<double>(const FwdArgs<double> *d_args, const int *d_prefix,
-                                         int n_surf, int total, int *d_counter, int cfg,
-                                         int n_ctas, cudaStream_t s) {
-  const FwdConfig c = fwd_config(true, cfg);
-  const size_t smem = (size_t)c.warps * c.obs_per_warp * c.win * sizeof(double);
-  if (c.tk == 2 && c.warps == 8)
-    return launch_batch_tk_nw<double, 2, 8>(d_args, d_prefix, n_surf, total, d_counter, smem,
-                                            n_ctas, s);
-  if (c.tk == 2 && c.warps == 4)
-    return launch_batch_tk_nw<double, 2, 4>(d_args, d_prefix, n_surf, total, d_counter, smem,
-                                            n_ctas, s);
-  if (c.tk == 1 && c.warps == 8)
-    return launch_batch_tk_nw<double, 1, 8>(d_args, d_prefix, n_surf, total, d_counter, smem,
-                                            n_ctas, s);
-  return cudaErrorInvalidValue;
+template <typename T>
+cudaError_t launch_plan(T *coef, const int *set_begin, int nsets, int O, int slack,
+                        int *i0max_tab, int *err, cudaStream_t s) {
+  if (nsets <= 0 || O <= 0) return cudaSuccess;
+  k_plan<T><<<nsets, 128, 0, s>>>(coef, set_begin, O, slack, i0max_tab, err);
+  return cudaGetLastError();
 }
+
+template cudaError_t launch_plan<float>(float *, const int *, int, int, int, int *, int *,
+                                        cudaStream_t);
+template cudaError_t launch_plan<double>(double *, const int *, int, int, int, int *, int *,
+                                         cudaStream_t);
+template cudaError_t launch_forward<float>(const FwdArgs<float> &, int, cudaStream_t);
+template cudaError_t launch_forward<double>(const FwdArgs<double> &, int, cudaStream_t);
+template cudaError_t launch_forward_batch<float>(const FwdArgs<float> *, const int *, int, int,
+                                                 int *, int, int, cudaStream_t);
+template cudaError_t launch_forward_batch<double>(const FwdArgs<double> *, const int *, int,
+                                                  int, int *, int, int, cudaStream_t);
 
 }  // namespace fwh

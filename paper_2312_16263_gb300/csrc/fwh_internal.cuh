@@ -10,9 +10,11 @@
 //                            rows >= nt are zero
 //   coef     [P][O][16] T    per (panel, observer): 8 integrand coefficients
 //                            (same order as X), then the interpolation
-//                            weights a, b, cc, dd and the integer shift i0
-//                            (bit pattern in slot 12 for float, value for
-//                            double), slots 13..15 unused
+//                            weights a, b, cc, dd, the integer shift i0
+//                            (slot 12) and the window offset i0max(set) - i0
+//                            written by the planner (slot 13); integers are
+//                            stored as bit patterns for float, as values for
+//                            double; slots 14..15 unused
 //   p_out    [O][nt] double  caller's output
 #pragma once
 
@@ -62,11 +64,13 @@ struct PrepArgs {
 
 template <typename T>
 struct FwdArgs {
+  const void *tmX;      // device CUtensorMap over X as [P*ntp rows][16] (TMA pipeline)
   const T *X;           // [P][ntp][16]
   const T *coef;        // [P][O][16]
   double *p_out;        // [O][nt]
   const int *n_valid;   // [O]
   const int *set_begin; // [nsets + 1] panel-set boundaries (sorted order)
+  const int *i0max_tab; // [nsets][O] largest shift of each (panel set, observer)
   int *err;
   int nsets, O, ntp, nt;
   int obs_per_cta, n_obs_groups;
@@ -109,16 +113,33 @@ cudaError_t launch_adjoint(const AdjArgs<T> &a, cudaStream_t s);
 
 // Forward tile configurations (index into a table in fwh_forward.cu).
 struct FwdConfig {
+  int pipe;           // 0: direct loads, 1: TMA + mbarrier pipeline (producer warp)
   int tk;             // source samples per lane per chunk (chunk = 32 tk)
-  int warps;          // warps per CTA
+  int warps;          // compute warps per CTA
   int obs_per_warp;   // max observers per warp
   int win;            // window slots per observer
   int seg_chunks;     // chunks per time segment
+  int stages;         // pipeline stages (pipe = 1)
+  int acc;            // 0: one sample per lane per block, 3: packed FP32x2 sample pairs
+  int wide;           // 1: register cap 200 instead of the occupancy launch bound
 };
+// Bytes of dynamic shared memory a config needs for `obs_per_cta` observers.
+size_t fwd_smem_bytes(bool fp64, const FwdConfig &c, int obs_per_cta);
+// Encode the TMA descriptor of X ([rows][16] elements of 4 or 8 bytes) into a
+// host buffer of 128 bytes; returns false if the driver refuses.
+bool encode_x_tensor_map(void *out128, const void *X, unsigned long long rows, bool fp64,
+                         int box_rows);
 int fwd_num_configs(bool fp64);
 FwdConfig fwd_config(bool fp64, int idx);
 template <typename T>
 cudaError_t launch_forward(const FwdArgs<T> &a, int cfg_idx, cudaStream_t s);
+// Planner kernel: per (panel set, observer) the largest shift i0max into
+// i0max_tab and, per record, the window offset i0max - i0 clamped to
+// [0, slack] (slack = win - chunk - 1) into slot 13; a set whose shifts span
+// more than slack raises kErrWindow.
+template <typename T>
+cudaError_t launch_plan(T *coef, const int *set_begin, int nsets, int O, int slack,
+                        int *i0max_tab, int *err, cudaStream_t s);
 
 // Batched persistent forward.
 template <typename T>

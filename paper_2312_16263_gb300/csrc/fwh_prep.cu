@@ -59,12 +59,18 @@ template <> __device__ __forceinline__ double inv_piv<double>(int j) {
   return c_inv_piv_d[j < kPivTab ? j : kPivTab - 1];
 }
 
-constexpr int kPanelsPerCta = 16;
+constexpr int kPanelsPerCta = 16;     // adjoint-prep tile
 constexpr int kThreads = kPanelsPerCta * 8;
 
 template <typename T> struct PrepChunk;
 template <> struct PrepChunk<float> { static constexpr int v = 128; };
 template <> struct PrepChunk<double> { static constexpr int v = 64; };
+
+// Forward-prep tile: lanes map to panels for coalesced field loads (128 bytes
+// of one field component per warp-row), then to (panel, series) pairs.
+template <typename T> struct PrepTile;
+template <> struct PrepTile<float> { static constexpr int panels = 32, chunk = 128; };
+template <> struct PrepTile<double> { static constexpr int panels = 16, chunk = 64; };
 
 // Integrand `which` (0: Qn, 1..3: L_c) of panel po at sample i.
 template <typename T>
@@ -84,78 +90,174 @@ struct Integrand {
   }
 };
 
-// Series value F_s(i): the integrand or its second-order FD derivative.
-template <typename T>
-__device__ __forceinline__ T series_at(const Integrand<T> &g, bool deriv, int i, int nt,
-                                       T inv2h) {
-  if (!deriv) return g(i);
-  if (i == 0) return (T(-3) * g(0) + T(4) * g(1) - g(2)) * inv2h;
-  if (i == nt - 1) return (T(3) * g(nt - 1) - T(4) * g(nt - 2) + g(nt - 3)) * inv2h;
-  return (g(i + 1) - g(i - 1)) * inv2h;
+// Element (sample i, value q) of a panel's X rows.  FP32 rows are stored with
+// sample pairs interleaved, [i/2][q][i&1], so one 16-byte load yields the
+// same two values of samples 2j and 2j+1 (the packed FP32x2 operands of the
+// forward kernel); FP64 rows are plain [i][q].
+template <typename T> __device__ __forceinline__ size_t xidx(int i, int q);
+template <> __device__ __forceinline__ size_t xidx<float>(int i, int q) {
+  return ((size_t)(i >> 1) * kRec + q) * 2 + (i & 1);
+}
+template <> __device__ __forceinline__ size_t xidx<double>(int i, int q) {
+  return (size_t)i * kRec + q;
 }
 
+// Forward prep.  Phase A stages the four integrands Qn, L_1..3 of the tile's
+// panels over the window (plus one sample each side for the FD stencil) in
+// shared memory, [row][integrand][panel], computed from coalesced field
+// loads.  Phase B runs one thread per (panel, series): the series value (the
+// integrand or its FD derivative), the forward elimination of the windowed
+// moment system and the back substitution.  Elimination values of the chunk
+// wait in the moment slots of X itself (re-read by the same thread), those of
+// the right halo in shared memory.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_prep(PrepArgs<T> a) {
+__global__ void __launch_bounds__(PrepTile<T>::panels * 8) k_prep(PrepArgs<T> a) {
+  constexpr int NP = PrepTile<T>::panels;
+  constexpr int NT = NP * 8;
+  constexpr int H = Prec<T>::halo;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *zbuf = reinterpret_cast<T *>(smem_raw);
   const int tid = threadIdx.x;
-  const int s = tid & 7;
-  const int p = blockIdx.x * kPanelsPerCta + (tid >> 3);
-  if (p >= a.P) return;
+  const int p0 = blockIdx.x * NP;
   const int c0 = blockIdx.y * a.chunk;
   const int c1 = min(c0 + a.chunk, a.ntp);
   const int nt = a.nt;
-  T *Xp = a.X + (size_t)p * a.ntp * kRec;
 
-  // zero rows beyond the record
-  for (int i = max(c0, nt); i < c1; ++i) {
-    Xp[(size_t)i * kRec + s] = T(0);
-    Xp[(size_t)i * kRec + 8 + s] = T(0);
+  if (c0 >= nt) {  // chunk past the record: zero rows
+    for (int idx = tid; idx < NP * (c1 - c0) * kRec; idx += NT) {
+      const int pl = idx / ((c1 - c0) * kRec);
+      const int r = idx % ((c1 - c0) * kRec);
+      if (p0 + pl < a.P) a.X[((size_t)(p0 + pl) * a.ntp + c0) * kRec + r] = T(0);
+    }
+    return;
   }
-  if (c0 >= nt) return;
   const int ce = min(c1, nt);
+  const int wa = max(0, c0 - H), wb = min(nt, ce + H);
+  const int ra = max(0, wa - 1), rb = min(nt, wb + 1);  // integrand rows
+  T *sb = reinterpret_cast<T *>(smem_raw);              // [rb - ra][4][NP]
+  T *zh = sb + (size_t)(rb - ra) * 4 * NP;              // [H][NT] right-halo z
 
-  Integrand<T> g;
-  g.f = a.fields;
-  g.P = a.P;
-  g.po = a.perm ? a.perm[p] : p;
-  g.n0 = (T)a.n[3 * p];
-  g.n1 = (T)a.n[3 * p + 1];
-  g.n2 = (T)a.n[3 * p + 2];
-  g.Un = (T)(a.ca * a.n[3 * p] + a.sa * a.n[3 * p + 1]);
+  // ---- phase A: integrands ---------------------------------------------------
+  {
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int RPW = 32 / NP;                        // rows per warp pass
+    const int pl = lane % NP;
+    const int p = p0 + pl;
+    const bool live = p < a.P;
+    const int po = live ? (a.perm ? a.perm[p] : p) : 0;
+    T n0 = 0, n1 = 0, n2 = 0, Un = 0;
+    if (live) {
+      n0 = (T)a.n[3 * p];
+      n1 = (T)a.n[3 * p + 1];
+      n2 = (T)a.n[3 * p + 2];
+      Un = (T)(a.ca * a.n[3 * p] + a.sa * a.n[3 * p + 1]);
+    }
+    const int stride = (NT / 32) * RPW;
+    auto integrands = [&](int i, T &q, T &l0, T &l1, T &l2) {
+      const T *b = a.fields + (size_t)i * 5 * a.P + po;
+      const T rho = b[0];
+      const T u0 = b[(size_t)a.P], u1 = b[2 * (size_t)a.P], u2 = b[3 * (size_t)a.P];
+      const T pp = b[4 * (size_t)a.P];
+      const T un = u0 * n0 + u1 * n1 + u2 * n2;
+      const T r1 = T(1) + rho;
+      const T utn = Un + un;
+      q = rho * Un + r1 * un;                 // Qn   (Eq. Qn_New_nd)
+      l0 = pp * n0 + r1 * u0 * utn;           // L_1  (Eq. Li_New_nd)
+      l1 = pp * n1 + r1 * u1 * utn;
+      l2 = pp * n2 + r1 * u2 * utn;
+    };
+    constexpr int U = 4;  // rows in flight per lane
+    for (int i0 = ra + warp * RPW + lane / NP; i0 < rb; i0 += U * stride) {
+      T q[U], l0[U], l1[U], l2[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * stride;
+        q[u] = l0[u] = l1[u] = l2[u] = T(0);
+        if (live && i < rb) integrands(i, q[u], l0[u], l1[u], l2[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * stride;
+        if (i < rb) {
+          T *row = sb + (size_t)(i - ra) * 4 * NP + pl;
+          row[0] = q[u];
+          row[NP] = l0[u];
+          row[2 * NP] = l1[u];
+          row[3 * NP] = l2[u];
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- phase B: series, forward elimination, back substitution ----------------
+  const int s = tid & 7;
+  const int pl = tid >> 3;
+  const int p = p0 + pl;
+  if (p >= a.P) return;
+  T *Xp = a.X + (size_t)p * a.ntp * kRec;
+  for (int i = max(c0, nt); i < c1; ++i) {  // rows past the record
+    Xp[xidx<T>(i, s)] = T(0);
+    Xp[xidx<T>(i, 8 + s)] = T(0);
+  }
   const bool deriv = (s == 0) || (s >= 2 && s <= 4);
-  g.which = (s <= 1) ? 0 : 1 + (s - 2) % 3;
-  g.nc = g.which == 1 ? g.n0 : (g.which == 2 ? g.n1 : g.n2);
+  const int q = (s <= 1) ? 0 : 1 + (s - 2) % 3;
+  const T *col = sb + q * NP + pl;  // integrand q of this panel, row stride 4 NP
+  auto B = [&](int i) -> T { return col[(size_t)(i - ra) * 4 * NP]; };
   const T inv2h = (T)(0.5 / a.dt);
   const T s6 = (T)(6.0 / (a.dt * a.dt));
-
-  constexpr int H = Prec<T>::halo;
-  const int wa = max(0, c0 - H), wb = min(nt, ce + H);
+  auto F = [&](int i) -> T {
+    if (!deriv) return B(i);
+    if (i == 0) return (T(-3) * B(0) + T(4) * B(1) - B(2)) * inv2h;
+    if (i == nt - 1) return (T(3) * B(nt - 1) - T(4) * B(nt - 2) + B(nt - 3)) * inv2h;
+    return (B(i + 1) - B(i - 1)) * inv2h;
+  };
   const int L = wb - wa;
-
-  T Fprev = T(0), Fcur = series_at(g, deriv, wa, nt, inv2h), z = T(0);
+  T Fprev = T(0), Fcur = F(wa), z = T(0);
+#pragma unroll 4
   for (int i = wa; i < wb; ++i) {
     const int j = i - wa;
-    const T Fnext = (i + 1 < wb) ? series_at(g, deriv, i + 1, nt, inv2h) : T(0);
-    if (i >= c0 && i < ce) Xp[(size_t)i * kRec + s] = Fcur;
+    const T Fnext = (i + 1 < wb) ? F(i + 1) : T(0);
+    if (i >= c0 && i < ce) Xp[xidx<T>(i, s)] = Fcur;
     if (j >= 1 && j <= L - 2) {
       const T r = s6 * (Fnext - T(2) * Fcur + Fprev);
       z = (r - z) * inv_piv<T>(j);
-      if (i >= c0) zbuf[(size_t)(i - c0) * kThreads + tid] = z;
+      if (i >= ce) {
+        zh[(size_t)(i - ce) * NT + tid] = z;
+      } else if (i >= c0) {
+        Xp[xidx<T>(i, 8 + s)] = z;
+      }
     }
     Fprev = Fcur;
     Fcur = Fnext;
   }
-  // back substitution over the chunk (+ right halo); m = 0 at window ends
   T mnext = T(0);
-  if (wb - 1 >= c0 && wb - 1 < ce) Xp[(size_t)(wb - 1) * kRec + 8 + s] = T(0);
-  for (int i = wb - 2; i >= c0 && i >= wa + 1; --i) {
-    const int j = i - wa;
-    const T m = zbuf[(size_t)(i - c0) * kThreads + tid] - mnext * inv_piv<T>(j);
-    if (i < ce) Xp[(size_t)i * kRec + 8 + s] = m;
+  if (wb - 1 >= c0 && wb - 1 < ce) Xp[xidx<T>(wb - 1, 8 + s)] = T(0);
+  const int ilo = max(c0, wa + 1);
+  int i = wb - 2;
+  // right halo (elimination values in shared memory)
+  for (; i >= ilo && i >= ce; --i) {
+    const T m = zh[(size_t)(i - ce) * NT + tid] - mnext * inv_piv<T>(i - wa);
     mnext = m;
   }
-  if (wa == c0) Xp[(size_t)c0 * kRec + 8 + s] = T(0);  // record start: m_0 = 0
+  // chunk: elimination values come back from X in blocks, loads issued first
+  constexpr int BB = 16;
+  for (; i - BB + 1 >= ilo; i -= BB) {
+    T zb[BB];
+#pragma unroll
+    for (int u = 0; u < BB; ++u) zb[u] = Xp[xidx<T>(i - u, 8 + s)];
+#pragma unroll
+    for (int u = 0; u < BB; ++u) {
+      const T m = zb[u] - mnext * inv_piv<T>(i - u - wa);
+      Xp[xidx<T>(i - u, 8 + s)] = m;
+      mnext = m;
+    }
+  }
+  for (; i >= ilo; --i) {
+    const T m = Xp[xidx<T>(i, 8 + s)] - mnext * inv_piv<T>(i - wa);
+    Xp[xidx<T>(i, 8 + s)] = m;
+    mnext = m;
+  }
+  if (wa == c0) Xp[xidx<T>(c0, 8 + s)] = T(0);  // record start: m_0 = 0
 }
 
 // ---------------------------------------------------------------------------
@@ -276,14 +378,18 @@ __global__ void __launch_bounds__(kThreads) k_prep_adj(PrepAdjArgs<T> a) {
 
 template <typename T>
 cudaError_t launch_prep(const PrepArgs<T> &a0, cudaStream_t s) {
+  constexpr int NP = PrepTile<T>::panels;
+  constexpr int H = Prec<T>::halo;
   PrepArgs<T> a = a0;
-  a.chunk = PrepChunk<T>::v;
-  const size_t smem = (size_t)(a.chunk + Prec<T>::halo) * kThreads * sizeof(T);
+  a.chunk = PrepTile<T>::chunk;
+  // integrand rows (chunk + 2 halos + 2 FD neighbours) x 4 x NP, plus the
+  // right-halo elimination values H x (NP * 8)
+  const size_t smem = ((size_t)(a.chunk + 2 * H + 2) * 4 * NP + (size_t)H * NP * 8) * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(k_prep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((a.P + kPanelsPerCta - 1) / kPanelsPerCta, (a.ntp + a.chunk - 1) / a.chunk);
-  k_prep<T><<<grid, kThreads, smem, s>>>(a);
+  dim3 grid((a.P + NP - 1) / NP, (a.ntp + a.chunk - 1) / a.chunk);
+  k_prep<T><<<grid, NP * 8, smem, s>>>(a);
   return cudaGetLastError();
 }
 
