@@ -50,8 +50,8 @@ __global__ void __launch_bounds__(256) k_adjoint(const T *coef, const T *Gt, T *
     const T *rec = rec0 + (size_t)o * kRec;
     T c[12];
 #pragma unroll
-    for (int s = 0; s < 12; ++s) c[s] = __ldg(rec + s);
-    const int i0 = i0_of<T>(__ldg(rec + 12));
+    for (int s = 0; s < 12; ++s) c[s] = __ldg(rec + s);  // c0..c7, a, b, cc, dd
+    const int i0 = i0_of<T>(__ldg(rec + slot::i0));
     const T *G = Gt + (size_t)o * ntp;
 #pragma unroll
     for (int j = 0; j < TK; ++j) {

@@ -1010,7 +1010,7 @@ fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, d
     nv[o] = (int)std::max(0.0, std::min((double)nt, v));
   }
   const std::vector<int> sets = build_sets(h->y, h->P, h->mach, h->dt, c.win - 32 * c.tk - 1);
-  const int ntp = (int)((nt + 127) / 128 * 128);
+  const int ntp = ntp0;                        // same padding as prepare_nt
   const int nsets = (int)sets.size() - 1;
   const size_t off_tm = round256((size_t)h->O * sizeof(int));
   const size_t off_sets = off_tm + 256;
@@ -1020,7 +1020,7 @@ fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, d
   if (need > cap)
     return fail(h, FWH_ERR_ARG,
                 "problem needs " + std::to_string(need) + " bytes of scratch (panels x nt rounded "
-                "up to 128 x 16 values + windows); the static scratch holds " +
+                "up to 256 x 16 values + windows); the static scratch holds " +
                     std::to_string(cap) + " bytes");
   int *d_nv = reinterpret_cast<int *>(scratch);
   int *d_sets = reinterpret_cast<int *>(scratch + off_sets);

@@ -63,17 +63,6 @@ template <> struct Vec<double> {
   static constexpr int per = 2;
 };
 
-template <typename T>
-__device__ __forceinline__ int rec_i0(const T *rec);
-template <>
-__device__ __forceinline__ int rec_i0<float>(const float *rec) {
-  return __float_as_int(__ldg(rec + 12));
-}
-template <>
-__device__ __forceinline__ int rec_i0<double>(const double *rec) {
-  return (int)__ldg(rec + 12);
-}
-
 template <typename T> __device__ __forceinline__ int rec_i0_of(T v);
 template <> __device__ __forceinline__ int rec_i0_of<float>(float v) {
   return __float_as_int(v);
@@ -156,14 +145,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// Test the phase; a thread whose phase is not complete is suspended until it
+// completes or kSuspendNs pass, so waiting warps do not spin on issue slots.
+constexpr unsigned kSuspendNs = 200000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
   unsigned ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -174,6 +166,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int *e
   const long long t0 = clock64();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      atomicOr(err, kErrTimeout);
+      *abort = 1;
+      return false;
+    }
+  }
+}
+// The producer's wait for a free stage: it sleeps between polls, so that
+// while the compute warps work it takes almost no issue slots from the warps
+// that share its SM sub-partition.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, unsigned parity, int *err,
+                                                volatile int *abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  unsigned ns = 64;
+  for (;;) {
+    __nanosleep(ns);
+    if (mbar_try_wait(bar, parity)) return true;
+    if (ns < 512) ns <<= 1;
     if (*abort) return false;
     if (clock64() - t0 > kWaitCycles) {
       atomicOr(err, kErrTimeout);
@@ -217,7 +229,7 @@ __global__ void __launch_bounds__(128) k_plan(T *coef, const int *set_begin, int
   for (int o = threadIdx.x; o < O; o += blockDim.x) {
     int lo = 0x7fffffff, hi = -0x7fffffff;
     for (int p = pb; p < pe; ++p) {
-      const int i0 = rec_i0_of<T>(coef[((size_t)p * O + o) * kRec + 12]);
+      const int i0 = rec_i0_of<T>(coef[((size_t)p * O + o) * kRec + slot::i0]);
       lo = min(lo, i0);
       hi = max(hi, i0);
     }
@@ -225,8 +237,8 @@ __global__ void __launch_bounds__(128) k_plan(T *coef, const int *set_begin, int
     i0max_tab[(size_t)sidx * O + o] = hi;
     for (int p = pb; p < pe; ++p) {
       T *rec = coef + ((size_t)p * O + o) * kRec;
-      const int off = min(hi - rec_i0_of<T>(rec[12]), slack);
-      rec[13] = int_as_rec<T>(off);
+      const int off = min(hi - rec_i0_of<T>(rec[slot::i0]), slack);
+      rec[slot::off] = int_as_rec<T>(off);
     }
   }
 }
@@ -351,6 +363,7 @@ __device__ __forceinline__ void flush_tail(const FwdArgs<T> &a, const Item<T, NW
 template <typename T, int TK, int NW>
 __device__ __forceinline__ void process_item_direct(const FwdArgs<T> &a, int item, T *smem,
                                                     int *st) {
+  static_assert(sizeof(T) == 8, "scalar consumers read the 16-value FP64 record");
   constexpr int CH = 32 * TK;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
@@ -369,7 +382,7 @@ __device__ __forceinline__ void process_item_direct(const FwdArgs<T> &a, int ite
         const int o = it.o_begin + w + NW * m;
         T c[kRec];
         load16<T>(rec0 + (size_t)o * kRec, c);
-        T *wm = wwin + (m * a.win + 1 + lane + rec_i0_of<T>(c[13]));
+        T *wm = wwin + (m * a.win + 1 + lane + rec_i0_of<T>(c[slot::off]));
         accumulate<T, TK>(x, c, wm);
       }
     }
@@ -399,36 +412,48 @@ __device__ __forceinline__ void produce_item(const FwdArgs<T> &a, const Item<T, 
   const unsigned cbytes = (unsigned)((it.o_end - it.o_begin) * kRec * sizeof(T));
   const int np = it.p_end - it.p_begin;
   const int nsteps = np * ((it.k_end - it.k_begin) / CH);
-  auto src_x = [&](int idx) {
-    const int p = it.p_begin + idx % np;
-    const int k0 = it.k_begin + (idx / np) * CH;
-    return a.X + ((size_t)p * a.ntp + k0) * kRec;
+  // Step idx covers panel p_begin + idx % np, chunk k_begin + (idx / np) CH.
+  // Both cursors (the load and the L2 prefetch running ahead of it) advance
+  // incrementally: this lane's per-step work stays short, since it is on the
+  // critical path of every stage refill.
+  auto src_x = [&](int pp, int kc) {
+    return a.X + ((size_t)(it.p_begin + pp) * a.ntp + it.k_begin + kc * CH) * kRec;
   };
-  auto src_c = [&](int idx) {
-    const int p = it.p_begin + idx % np;
-    return a.coef + ((size_t)p * a.O + it.o_begin) * kRec;
+  auto src_c = [&](int pp) {
+    return a.coef + ((size_t)(it.p_begin + pp) * a.O + it.o_begin) * kRec;
   };
-  for (int idx = 0; idx < min(nsteps, ps.nst + kPrefetchSteps); ++idx) {
-    prefetch_l2(src_x(idx), ps.x_bytes);
-    prefetch_l2(src_c(idx), cbytes);
-  }
+  int fp = 0, fk = 0;  // prefetch cursor (panel offset, chunk)
+  auto prefetch_next = [&]() {
+    prefetch_l2(src_x(fp, fk), ps.x_bytes);
+    prefetch_l2(src_c(fp), cbytes);
+    if (++fp == np) {
+      fp = 0;
+      ++fk;
+    }
+  };
+  const int lead = min(nsteps, ps.nst + kPrefetchSteps);
+  for (int idx = 0; idx < lead; ++idx) prefetch_next();
+  int cp = 0, ck = 0;  // load cursor
+  unsigned s = step % (unsigned)ps.nst, ph = (step / (unsigned)ps.nst) & 1u;
   for (int idx = 0; idx < nsteps; ++idx, ++step) {
     if (*ps.abort) return;
-    const int pf = idx + ps.nst + kPrefetchSteps;
-    if (pf < nsteps) {
-      prefetch_l2(src_x(pf), ps.x_bytes);
-      prefetch_l2(src_c(pf), cbytes);
-    }
-    const int p = it.p_begin + idx % np;
-    const int k0 = it.k_begin + (idx / np) * CH;
-    const int s = (int)(step % (unsigned)ps.nst);
-    const unsigned ph = (step / (unsigned)ps.nst) & 1u;
-    if (step >= (unsigned)ps.nst && !mbar_wait(&ps.empty[s], ph ^ 1u, a.err, ps.abort)) return;
+    if (idx + lead < nsteps) prefetch_next();
+    if (step >= (unsigned)ps.nst && !mbar_wait_sleep(&ps.empty[s], ph ^ 1u, a.err, ps.abort))
+      return;
     unsigned char *dst = ps.stage0 + (size_t)s * ps.stage_bytes;
     mbar_expect_tx(&ps.full[s], ps.x_bytes + cbytes);
     // tensor rows are 128 bytes: two FP32 samples or one FP64 sample
-    tma_load_2d(dst, a.tmX, 0, (p * a.ntp + k0) / (sizeof(T) == 4 ? 2 : 1), &ps.full[s]);
-    bulk_load(dst + ps.x_bytes, src_c(idx), cbytes, &ps.full[s]);
+    const int row = (it.p_begin + cp) * a.ntp + it.k_begin + ck * CH;
+    tma_load_2d(dst, a.tmX, 0, sizeof(T) == 4 ? row >> 1 : row, &ps.full[s]);
+    bulk_load(dst + ps.x_bytes, src_c(cp), cbytes, &ps.full[s]);
+    if (++cp == np) {
+      cp = 0;
+      ++ck;
+    }
+    if (++s == (unsigned)ps.nst) {
+      s = 0;
+      ph ^= 1u;
+    }
   }
 }
 
@@ -436,6 +461,7 @@ template <typename T, int TK, int NW>
 __device__ __forceinline__ void consume_item(const FwdArgs<T> &a, const Item<T, NW> &it,
                                              const PipeState &ps, unsigned &step, T *wwin,
                                              int *s_i0max) {
+  static_assert(sizeof(T) == 8, "scalar consumers read the 16-value FP64 record");
   constexpr int CH = 32 * TK;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
@@ -454,7 +480,7 @@ __device__ __forceinline__ void consume_item(const FwdArgs<T> &a, const Item<T, 
         const int o = it.o_begin + w + NW * m;
         T c[kRec];
         lds16<T>(crec + (size_t)(o - it.o_begin) * kRec, c);
-        T *wm = wwin + (m * a.win + 1 + lane + rec_i0_of<T>(c[13]));
+        T *wm = wwin + (m * a.win + 1 + lane + rec_i0_of<T>(c[slot::off]));
         accumulate<T, TK>(x, c, wm);
       }
       __syncwarp();
@@ -465,144 +491,183 @@ __device__ __forceinline__ void consume_item(const FwdArgs<T> &a, const Item<T, 
   flush_tail<T, CH, NW>(a, it, w, wwin, s_i0max);
 }
 
-// ---- packed FP32x2 consumer (mixed precision) --------------------------------
-// FP32 X rows hold sample pairs interleaved ([k/2][value][k&1]), so the
-// 16-byte chunk c of pair row pi is the two packed operands
-// (x_{2pi}[2c], x_{2pi+1}[2c]) and (x_{2pi}[2c+1], x_{2pi+1}[2c+1]).  Lane l
-// owns pair rows pi = l + 32 t (samples k = k0 + 2 pi and k + 1) and computes
-// both samples' signal and moment with fma.rn.f32x2 (two FMAs per issued
-// instruction):  G = (g_k, g_k+1) = sum_q c_q X[q],  M likewise on the
-// moments, U = a G + cc M (left-node parts), V = b G + dd M (right-node
-// parts).  The bins are B0 = k - i0 - 1 (v_k), B1 = k - i0 (u_k + v_k+1) and
-// B2 = k - i0 + 1 (u_k+1); B0 of lane l is B2 of lane l - 1.  The slot
-// parity of B1 depends only on i0, so each lane updates one aligned pair with
-// a packed 64-bit read-modify-write:
-//  * B1 even: (B1, B2) += (u_k + v_k+1, u_k+1 + v_k+2 of lane l + 1); the bin
-//    below the chunk gets v_k of lane 0, block 0 separately;
-//  * B1 odd:  (B0, B1) += (v_k + u_k-1 of lane l - 1, u_k + v_k+1); the bin
-//    above the chunk gets u of lane 31, last block separately.
-// Within one (panel, observer) no two lanes touch the same bin; one
-// __syncwarp per panel orders the next panel's shifted updates.
-typedef unsigned long long u64;
-__device__ __forceinline__ u64 pk2(float lo, float hi) {
-  u64 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+// ---- FP32 consumer (mixed precision) ----------------------------------------
+// FP32 X rows pair the samples j and j + 32 of each 64-sample block, so the
+// 16-byte chunk c of pair row pi = 32 b + j holds (x_k[2c], x_k+32[2c],
+// x_k[2c+1], x_k+32[2c+1]), k = 64 b + j: one swizzled row read per lane
+// gives both samples' series.  Lane l owns pair rows pi = l + 32 t of a chunk
+// (samples s = 64 t + l and s + 32) and forms, per observer, G = sum_q c_q X_q
+// and M likewise on the moments, u = a G + cc M (left-node part) and v = b G
+// + dd M (right-node part), all as scalar FMAs (a packed fma.rn.f32x2 takes
+// two issue cycles, so it buys no throughput over FFMA here).  Sample s adds
+// u_s to window slot 1 + s + off and v_s to slot s + off, so slot 1 + s + off
+// receives u_s + v_s+1: lane l takes v_s+1 from lane l + 1 (lane 31 from lane
+// 0's other sample, or from lane 0 of block t + 1) and updates the slots of
+// its two samples, 32 apart, with 32-bit read-modify-writes whose old value
+// enters the u FMA.  Consecutive lanes touch consecutive slots: no bank
+// conflicts, and no dependence of the code path on the shift.  The slot below
+// the chunk (v_0) is added by lane 0 separately.  Within one (panel,
+// observer) no two lanes touch the same slot; one __syncwarp per panel
+// orders the next panel's shifted updates.
+// Shared-space accesses by 32-bit address (the packed consumer addresses the
+// stage ring and its windows explicitly, so no generic-address arithmetic).
+__device__ __forceinline__ int lds_s32(unsigned addr) {
+  int v;
+  asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ float lds_f32(unsigned addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts_f32(unsigned addr, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+// Read-modify-write add to one shared float by the lanes whose `on` is
+// nonzero, predicated (no branch).  Not atomic: the caller guarantees that no
+// other lane touches the address at the same time (a shared-memory atomic
+// here stalls the warp's later shared accesses).
+__device__ __forceinline__ void add_f32_if(unsigned addr, float v, unsigned on) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t.reg .f32 t;\n\t"
+      "setp.ne.u32 q, %2, 0;\n\t"
+      "@q ld.shared.f32 t, [%0];\n\t"
+      "@q add.f32 t, t, %1;\n\t"
+      "@q st.shared.f32 [%0], t;\n\t}" ::"r"(addr),
+      "f"(v), "r"(on)
+      : "memory");
+}
+
+// Loads of stage data (X rows, records): not volatile, so the compiler may
+// schedule them early; they stay after the stage's full-barrier wait because
+// their addresses derive from stage_token(), which that wait orders.
+__device__ __forceinline__ float4 lds_v4f32(unsigned addr) {
+  float4 v;
+  asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ int lds_s32_stage(unsigned addr) {
+  int v;
+  asm("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+// The stage address as an opaque value produced after the barrier wait.
+__device__ __forceinline__ unsigned stage_token(unsigned addr) {
+  unsigned r;
+  asm volatile("mov.u32 %0, %1;" : "=r"(r) : "r"(addr) : "memory");
   return r;
 }
-__device__ __forceinline__ void upk2(u64 r, float &lo, float &hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
-}
-__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c) {
-  u64 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ u64 fmul2(u64 a, u64 b) {
-  u64 d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ u64 fadd2(u64 a, u64 b) {
-  u64 d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
+
+// The first 14 slots of one FP32 record: c0..c7, a, b, cc, dd, i0, off.
+struct Coef {
+  float c[8], wa, wb, wcc, wdd;
+  int off;
+};
+__device__ __forceinline__ void lds_coef(unsigned rec, Coef &k) {
+  static_assert(slot::c == 0 && slot::a == 8 && slot::b == 9 && slot::cc == 10 &&
+                    slot::dd == 11 && slot::off == 13,
+                "record read as three 16-byte groups and one word");
+  const float4 c0 = lds_v4f32(rec), c1 = lds_v4f32(rec + 16), w = lds_v4f32(rec + 32);
+  k.c[0] = c0.x; k.c[1] = c0.y; k.c[2] = c0.z; k.c[3] = c0.w;
+  k.c[4] = c1.x; k.c[5] = c1.y; k.c[6] = c1.z; k.c[7] = c1.w;
+  k.wa = w.x; k.wb = w.y; k.wcc = w.z; k.wdd = w.w;
+  k.off = lds_s32_stage(rec + 4 * slot::off);
 }
 
-// Pair row pi of a SWIZZLE_128B stage (128-byte rows): chunk c at c ^ (pi & 7).
-__device__ __forceinline__ void lds_pair_row(const unsigned char *stg, int pi, u64 (&X)[kRec]) {
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const ulonglong2 v =
-        *reinterpret_cast<const ulonglong2 *>(stg + (size_t)pi * 128 + ((c ^ (pi & 7)) << 4));
-    X[2 * c] = v.x;
-    X[2 * c + 1] = v.y;
-  }
-}
-
-template <int TK, int NW>
-__device__ __forceinline__ void consume_item_f32x2(const FwdArgs<float> &a,
-                                                   const Item<float, NW> &it,
-                                                   const PipeState &ps, unsigned &step,
-                                                   float *wwin, int *s_i0max) {
+template <int TK, int NW, bool PF>
+__device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
+                                                 const Item<float, NW> &it,
+                                                 const PipeState &ps, unsigned &step,
+                                                 float *wwin, int *s_i0max) {
   constexpr int CH = 32 * TK;
   constexpr int NP = TK / 2;  // pair rows per lane
+  constexpr unsigned RB = kRec * 4;  // record bytes
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   item_prologue<float, NW>(a, it, w, wwin, s_i0max);
+  // Window of observer m starts at win_s + m * win_b; lane l's slot for its
+  // block-t samples is 1 + 64 t + l (+ 32) + off.
+  const unsigned win_b = (unsigned)a.win * 4u;
+  const unsigned win_s = smem_u32(wwin) + (1u + (unsigned)lane) * 4u;
+  const unsigned stage0 = smem_u32(ps.stage0);
+  // X pair row pi = lane + 32 t of a stage: 16-byte chunk c at c ^ (lane & 7).
+  const unsigned xrow = (unsigned)lane * 128u;
+  const unsigned xswz = ((unsigned)lane & 7u) << 4;
+  const bool last = lane == 31;
+  const unsigned first = lane == 0;
+  unsigned s = step % (unsigned)ps.nst, ph = (step / (unsigned)ps.nst) & 1u;
   for (int k0 = it.k_begin; k0 < it.k_end; k0 += CH) {
     for (int p = it.p_begin; p < it.p_end; ++p, ++step) {
-      const int s = (int)(step % (unsigned)ps.nst);
-      const unsigned ph = (step / (unsigned)ps.nst) & 1u;
       if (!mbar_wait(&ps.full[s], ph, a.err, ps.abort)) return;
-      const unsigned char *stg = ps.stage0 + (size_t)s * ps.stage_bytes;
-      u64 X[NP][kRec];
+      const unsigned stg = stage_token(stage0 + s * ps.stage_bytes);
+      float X[NP][2][kRec];  // [pair row][sample s, s + 32][value]
 #pragma unroll
-      for (int t = 0; t < NP; ++t) lds_pair_row(stg, lane + 32 * t, X[t]);
-      const float *crec = reinterpret_cast<const float *>(stg + ps.x_bytes) + (size_t)w * kRec;
-      float c[kRec];
-      if (it.nobs > 0) lds16<float>(crec, c);
+      for (int t = 0; t < NP; ++t) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float4 v = lds_v4f32(stg + xrow + 4096u * t + (((unsigned)c << 4) ^ xswz));
+          X[t][0][2 * c] = v.x;
+          X[t][1][2 * c] = v.y;
+          X[t][0][2 * c + 1] = v.z;
+          X[t][1][2 * c + 1] = v.w;
+        }
+      }
+      const unsigned crec = stg + ps.x_bytes + (unsigned)w * RB;
+      // PF: read the next observer's record while this one computes, else
+      // read each record right before its use.
+      Coef k;
+      if (PF && it.nobs > 0) lds_coef(crec, k);
       for (int m = 0; m < it.nobs; ++m) {
-        float *w1 = wwin + (m * a.win + 1 + 2 * lane + rec_i0_of<float>(c[13]));
-        const bool even = ((reinterpret_cast<uintptr_t>(w1) >> 2) & 1) == 0;
-        float *w64 = even ? w1 : w1 - 1;
-        u64 old[NP];
+        if (!PF) lds_coef(crec + (unsigned)m * NW * RB, k);
+        const unsigned w1 = win_s + (unsigned)m * win_b + (unsigned)k.off * 4u;
+        float u[NP][2], v[NP][2];
 #pragma unroll
-        for (int t = 0; t < NP; ++t) old[t] = *reinterpret_cast<const u64 *>(w64 + 64 * t);
-        float cn[kRec];
-        if (m + 1 < it.nobs) lds16<float>(crec + (size_t)(m + 1) * NW * kRec, cn);
-        u64 U[NP], V[NP];
+        for (int t = 0; t < NP; ++t)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) u[t][h] = lds_f32(w1 + 256u * t + 128u * h);
 #pragma unroll
         for (int t = 0; t < NP; ++t) {
-          u64 G = fmul2(pk2(c[0], c[0]), X[t][0]);
-          u64 M = fmul2(pk2(c[0], c[0]), X[t][8]);
 #pragma unroll
-          for (int q = 1; q < 8; ++q) {
-            const u64 cq = pk2(c[q], c[q]);
-            G = ffma2(cq, X[t][q], G);
-            M = ffma2(cq, X[t][8 + q], M);
+          for (int h = 0; h < 2; ++h) {
+            float G = k.c[0] * X[t][h][0];
+            float M = k.c[0] * X[t][h][8];
+#pragma unroll
+            for (int q = 1; q < 8; ++q) {
+              G = fmaf(k.c[q], X[t][h][q], G);
+              M = fmaf(k.c[q], X[t][h][8 + q], M);
+            }
+            u[t][h] = fmaf(k.wcc, M, fmaf(k.wa, G, u[t][h]));  // old slot value + u
+            v[t][h] = fmaf(k.wdd, M, k.wb * G);
           }
-          U[t] = ffma2(pk2(c[10], c[10]), M, fmul2(pk2(c[8], c[8]), G));
-          V[t] = ffma2(pk2(c[11], c[11]), M, fmul2(pk2(c[9], c[9]), G));
         }
-        if (even) {
-          float va[NP], vb[NP], sv[NP];
+        Coef kn;
+        if (PF && m + 1 < it.nobs) lds_coef(crec + (unsigned)(m + 1) * NW * RB, kn);
+        float sv[NP][2];
 #pragma unroll
-          for (int t = 0; t < NP; ++t) {
-            upk2(V[t], va[t], vb[t]);
-            sv[t] = __shfl_sync(0xffffffffu, va[t], (lane + 1) & 31);
-          }
+        for (int t = 0; t < NP; ++t)
 #pragma unroll
-          for (int t = 0; t < NP; ++t) {
-            // lane 31's B2 is lane 0's B0 of the next block (none after the last)
-            const float ex = lane < 31 ? sv[t] : (t + 1 < NP ? sv[t + 1 < NP ? t + 1 : t] : 0.f);
-            const u64 wv = fadd2(U[t], pk2(vb[t], ex));
-            *reinterpret_cast<u64 *>(w64 + 64 * t) = fadd2(old[t], wv);
-          }
-          if (lane == 0) w1[-1] += va[0];  // bin below the chunk
-        } else {
-          float ua[NP], ub[NP], va[NP], vb[NP], su[NP];
+          for (int h = 0; h < 2; ++h) sv[t][h] = __shfl_sync(0xffffffffu, v[t][h], (lane + 1) & 31);
 #pragma unroll
-          for (int t = 0; t < NP; ++t) {
-            upk2(U[t], ua[t], ub[t]);
-            upk2(V[t], va[t], vb[t]);
-            su[t] = __shfl_sync(0xffffffffu, ub[t], (lane + 31) & 31);
-          }
-#pragma unroll
-          for (int t = 0; t < NP; ++t) {
-            // lane 0's B0 is lane 31's B2 of the previous block (none before the first)
-            const float ex = lane > 0 ? su[t] : (t > 0 ? su[t > 0 ? t - 1 : t] : 0.f);
-            const u64 wv = fadd2(pk2(va[t], ua[t]), pk2(ex, vb[t]));
-            *reinterpret_cast<u64 *>(w64 + 64 * t) = fadd2(old[t], wv);
-          }
-          if (lane == 31) w1[64 * (NP - 1) + 1] += ub[NP - 1];  // bin above the chunk
+        for (int t = 0; t < NP; ++t) {
+          // v of the sample after each of the lane's two: lane l + 1's, and
+          // for lane 31 lane 0's other sample / lane 0 of the next block
+          const float e0 = last ? sv[t][1] : sv[t][0];
+          const float e1 = last ? (t + 1 < NP ? sv[t + 1 < NP ? t + 1 : t][0] : 0.f) : sv[t][1];
+          sts_f32(w1 + 256u * t, u[t][0] + e0);
+          sts_f32(w1 + 256u * t + 128u, u[t][1] + e1);
         }
-        if (m + 1 < it.nobs) {
-#pragma unroll
-          for (int q = 0; q < kRec; ++q) c[q] = cn[q];
-        }
+        add_f32_if(w1 - 4u, v[0][0], first);  // slot below the chunk (lane 0 only)
+        if (PF && m + 1 < it.nobs) k = kn;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&ps.empty[s]);
+      if (++s == (unsigned)ps.nst) {
+        s = 0;
+        ph ^= 1u;
+      }
     }
     flush_slide<float, CH, NW>(a, it, w, wwin, s_i0max, k0);
   }
@@ -677,8 +742,8 @@ __device__ __forceinline__ void forward_cta(const FwdArgs<T> &a, int nst) {
     } else {
       const Item<T, NW> it(a, blockIdx.x, w);
       T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.win;
-      if constexpr (ACC == 3 && sizeof(T) == 4) {
-        consume_item_f32x2<TK, NW>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
+      if constexpr (ACC >= 3 && sizeof(T) == 4) {
+        consume_item_f32<TK, NW, ACC == 4>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
       } else {
         consume_item<T, TK, NW>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
       }
@@ -702,11 +767,8 @@ __global__ void __maxnreg__(200) k_forward_wide(FwdArgs<T> a, int nst) {
 
 // Persistent form: CTAs pull work items of several surfaces from one queue.
 template <typename T, int TK, int NW, int PIPE, int ACC>
-__global__ void __launch_bounds__((NW + PIPE) * 32, (MinBlocks<TK, NW, PIPE>::v)) k_forward_batch(
-    const FwdArgs<T> *args,
-                                                                     const int *item_prefix,
-                                                                     int n_surf, int total,
-                                                                     int *counter, int nst) {
+__device__ __forceinline__ void forward_batch_cta(const FwdArgs<T> *args, const int *item_prefix,
+                                                  int n_surf, int total, int *counter, int nst) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int st[NW * kMaxObsPerWarp];
   __shared__ int s_item;
@@ -746,8 +808,9 @@ __global__ void __launch_bounds__((NW + PIPE) * 32, (MinBlocks<TK, NW, PIPE>::v)
       } else {
         const Item<T, NW> it(a, li, w);
         T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.win;
-        if constexpr (ACC == 3 && sizeof(T) == 4) {
-          consume_item_f32x2<TK, NW>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
+        if constexpr (ACC >= 3 && sizeof(T) == 4) {
+          consume_item_f32<TK, NW, ACC == 4>(a, it, ps, step, wwin,
+                                               st + w * kMaxObsPerWarp);
         } else {
           consume_item<T, TK, NW>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
         }
@@ -759,15 +822,32 @@ __global__ void __launch_bounds__((NW + PIPE) * 32, (MinBlocks<TK, NW, PIPE>::v)
   }
 }
 
-// Candidate tile shapes {pipe, tk, warps, obs_per_warp, win, seg_chunks, stages}.
-// acc: 0 one sample per lane per block (FP64), 3 packed FP32x2 sample pairs
-// (FP32; the FP32 series layout is pair-interleaved, so every FP32 shape is a
-// TMA shape).
+template <typename T, int TK, int NW, int PIPE, int ACC>
+__global__ void __launch_bounds__((NW + PIPE) * 32, (MinBlocks<TK, NW, PIPE>::v))
+    k_forward_batch(const FwdArgs<T> *args, const int *item_prefix, int n_surf, int total,
+                    int *counter, int nst) {
+  forward_batch_cta<T, TK, NW, PIPE, ACC>(args, item_prefix, n_surf, total, counter, nst);
+}
+
+template <typename T, int TK, int NW, int PIPE, int ACC>
+__global__ void __maxnreg__(200)
+    k_forward_batch_wide(const FwdArgs<T> *args, const int *item_prefix, int n_surf, int total,
+                         int *counter, int nst) {
+  forward_batch_cta<T, TK, NW, PIPE, ACC>(args, item_prefix, n_surf, total, counter, nst);
+}
+
+// Candidate tile shapes {pipe, tk, warps, obs_per_warp, win, seg_chunks,
+// stages, acc, wide}.  acc: 0 one sample per lane per block (FP64), 3 two
+// samples 32 apart per lane per block (FP32; its series rows pair those
+// samples, so every FP32 shape is a TMA shape), 4 the same with the next
+// observer's record read ahead.  wide: register cap 200 instead of the launch
+// bounds' occupancy target.  Register use (ptxas, sm_103a): tk 4 shapes 126
+// to 128 (three CTAs of five warps per SM), tk 8 168 (two).
 const FwdConfig kCfgF32[] = {
     {1, 4, 4, 9, 224, 4, 3, 3, 0},
-    {1, 4, 4, 9, 224, 4, 6, 3, 1},
-    {1, 4, 8, 9, 224, 4, 4, 3, 1},
-    {1, 8, 4, 9, 352, 2, 4, 3, 1},
+    {1, 4, 4, 9, 224, 4, 3, 4, 0},
+    {1, 4, 4, 8, 224, 4, 3, 3, 0},
+    {1, 8, 4, 9, 352, 2, 3, 3, 0},
 };
 const FwdConfig kCfgF64[] = {
     {0, 2, 8, 16, 128, 8, 0, 0, 0},
@@ -782,7 +862,8 @@ size_t smem_for(const FwdConfig &c, int obs_per_cta) {
   size_t win = (size_t)c.warps * opw * c.win * sizeof(T);
   if (c.pipe == 0) return win;
   const size_t xb = (size_t)32 * c.tk * kRec * sizeof(T);
-  const size_t sb = (xb + (size_t)obs_per_cta * kRec * sizeof(T) + 1023) & ~size_t(1023);
+  const size_t sb =
+      (xb + (size_t)obs_per_cta * kRec * sizeof(T) + 1023) & ~size_t(1023);
   return 1024 + (size_t)c.stages * sb + win;
 }
 
@@ -801,13 +882,14 @@ cudaError_t launch_one(const FwdArgs<T> &a, const FwdConfig &c, cudaStream_t s) 
 
 template <typename T, int TK, int NW, int PIPE, int ACC>
 cudaError_t launch_batch_one(const FwdArgs<T> *d_args, const int *d_prefix, int n_surf,
-                             int total, int *d_counter, size_t smem, int n_ctas, int nst,
-                             cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_forward_batch<T, TK, NW, PIPE, ACC>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                             int total, int *d_counter, size_t smem, int n_ctas, bool wide,
+                             int nst, cudaStream_t s) {
+  auto kern = wide ? k_forward_batch_wide<T, TK, NW, PIPE, ACC>
+                   : k_forward_batch<T, TK, NW, PIPE, ACC>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_forward_batch<T, TK, NW, PIPE, ACC><<<n_ctas, (NW + PIPE) * 32, smem, s>>>(
-      d_args, d_prefix, n_surf, total, d_counter, nst);
+  kern<<<n_ctas, (NW + PIPE) * 32, smem, s>>>(d_args, d_prefix, n_surf, total, d_counter, nst);
   return cudaGetLastError();
 }
 
@@ -861,8 +943,8 @@ bool encode_x_tensor_map(void *out128, const void *X, unsigned long long rows, b
 #define FWH_DISPATCH(T, c, CALL)                                                        \
   do {                                                                                   \
     if constexpr (sizeof(T) == 4) {                                                      \
-      if (c.pipe == 1 && c.tk == 4 && c.warps == 8 && c.acc == 3) return CALL(T, 4, 8, 1, 3); \
       if (c.pipe == 1 && c.tk == 4 && c.warps == 4 && c.acc == 3) return CALL(T, 4, 4, 1, 3); \
+      if (c.pipe == 1 && c.tk == 4 && c.warps == 4 && c.acc == 4) return CALL(T, 4, 4, 1, 4); \
       if (c.pipe == 1 && c.tk == 8 && c.warps == 4 && c.acc == 3) return CALL(T, 8, 4, 1, 3); \
     } else {                                                                             \
       if (c.pipe == 0 && c.tk == 2 && c.warps == 8) return CALL(T, 2, 8, 0, 0);          \
@@ -889,7 +971,7 @@ cudaError_t launch_forward_batch(const FwdArgs<T> *d_args, const int *d_prefix, 
   const size_t smem = smem_for<T>(c, c.warps * c.obs_per_warp);
 #define FWH_CALL_BATCH(TT, TK, NW, PIPE, ACC)                                          \
   launch_batch_one<TT, TK, NW, PIPE, ACC>(d_args, d_prefix, n_surf, total, d_counter, smem, \
-                                          n_ctas, c.stages, s)
+                                          n_ctas, c.wide != 0, c.stages, s)
   FWH_DISPATCH(T, c, FWH_CALL_BATCH);
 #undef FWH_CALL_BATCH
 }

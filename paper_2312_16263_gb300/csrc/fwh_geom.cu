@@ -72,12 +72,12 @@ __global__ void __launch_bounds__(256) k_window(GeomArgs a) {
 template <typename T>
 __device__ __forceinline__ void store_i0(T *rec, int i0);
 template <>
-__device__ __forceinline__ void store_i0<float>(float *rec, int i0) {
-  rec[12] = __int_as_float(i0);
+__device__ __forceinline__ void store_i0<float>(float *slot, int i0) {
+  *slot = __int_as_float(i0);
 }
 template <>
-__device__ __forceinline__ void store_i0<double>(double *rec, int i0) {
-  rec[12] = (double)i0;
+__device__ __forceinline__ void store_i0<double>(double *slot, int i0) {
+  *slot = (double)i0;
 }
 
 template <typename T>
@@ -112,15 +112,15 @@ __global__ void __launch_bounds__(128) k_coef(GeomArgs a, T *coef) {
   const double aw = 1.0 - f, bw = f;
   const double h26 = a.dt * a.dt / 6.0;
   T *rec = coef + ((size_t)p * a.O + o) * kRec;
-  for (int i = 0; i < 8; ++i) rec[i] = (T)c[i];
-  rec[8] = (T)aw;
-  rec[9] = (T)bw;
-  rec[10] = (T)((aw * aw * aw - aw) * h26);
-  rec[11] = (T)((bw * bw * bw - bw) * h26);
-  store_i0<T>(rec, (int)fl);
-  rec[13] = (T)0;
+  for (int i = 0; i < 8; ++i) rec[slot::c + i] = (T)c[i];
+  rec[slot::a] = (T)aw;
+  rec[slot::b] = (T)bw;
+  rec[slot::cc] = (T)((aw * aw * aw - aw) * h26);
+  rec[slot::dd] = (T)((bw * bw * bw - bw) * h26);
+  rec[slot::off] = (T)0;
   rec[14] = (T)0;
   rec[15] = (T)0;
+  store_i0<T>(rec + slot::i0, (int)fl);
 }
 
 }  // namespace

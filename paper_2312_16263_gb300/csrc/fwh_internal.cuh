@@ -7,14 +7,16 @@
 //                            observer-independent series
 //                              0 Qn_dot 1 Qn 2..4 L_dot 5..7 L
 //                            then their natural-spline moments (8..15);
-//                            rows >= nt are zero
-//   coef     [P][O][16] T    per (panel, observer): 8 integrand coefficients
-//                            (same order as X), then the interpolation
-//                            weights a, b, cc, dd, the integer shift i0
-//                            (slot 12) and the window offset i0max(set) - i0
-//                            written by the planner (slot 13); integers are
-//                            stored as bit patterns for float, as values for
-//                            double; slots 14..15 unused
+//                            rows >= nt are zero.  FP32 X pairs samples j
+//                            and j + 32 of every 64-sample block in one
+//                            128-byte row, [ntp/64][32][16][2]
+//   coef     [P][O][16] T    per (panel, observer) record (slots in
+//                            namespace slot): the 8 integrand coefficients
+//                            (same order as X), the interpolation weights
+//                            a, b, cc, dd, the integer shift i0 and the
+//                            window offset i0max(set) - i0 written by the
+//                            planner; integers are bit patterns in FP32
+//                            records, values in FP64 ones
 //   p_out    [O][nt] double  caller's output
 #pragma once
 
@@ -24,6 +26,14 @@
 namespace fwh {
 
 constexpr int kRec = 16;          // values per X row and per coef record
+
+// Slots of a coefficient record (kRec values, both precisions).
+namespace slot {
+constexpr int c = 0;    // c0..c7: coefficients of the eight series
+constexpr int a = 8, b = 9, cc = 10, dd = 11;  // interpolation weights
+constexpr int i0 = 12;  // integer shift (bit pattern in FP32 records)
+constexpr int off = 13; // window offset i0max(set) - i0, written by the planner
+}  // namespace slot
 constexpr int kWarp = 32;
 
 // Halo (samples) of the windowed natural-spline solves: the influence of a
@@ -120,7 +130,8 @@ struct FwdConfig {
   int win;            // window slots per observer
   int seg_chunks;     // chunks per time segment
   int stages;         // pipeline stages (pipe = 1)
-  int acc;            // 0: one sample per lane per block, 3: packed FP32x2 sample pairs
+  int acc;            // 0: one sample per lane per block, 3: FP32 sample pairs 32 apart,
+                      // 4: packed with the next record read ahead
   int wide;           // 1: register cap 200 instead of the occupancy launch bound
 };
 // Bytes of dynamic shared memory a config needs for `obs_per_cta` observers.

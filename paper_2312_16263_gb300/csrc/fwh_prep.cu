@@ -90,13 +90,14 @@ struct Integrand {
   }
 };
 
-// Element (sample i, value q) of a panel's X rows.  FP32 rows are stored with
-// sample pairs interleaved, [i/2][q][i&1], so one 16-byte load yields the
-// same two values of samples 2j and 2j+1 (the packed FP32x2 operands of the
-// forward kernel); FP64 rows are plain [i][q].
+// Element (sample i, value q) of a panel's X rows.  FP32 rows pair the
+// samples j and j + 32 of each 64-sample block: row 32 (i / 64) + i % 32
+// holds [q][(i / 32) & 1], so one 16-byte load yields the same two values of
+// both samples (the packed FP32x2 operands of the forward kernel); FP64 rows
+// are plain [i][q].
 template <typename T> __device__ __forceinline__ size_t xidx(int i, int q);
 template <> __device__ __forceinline__ size_t xidx<float>(int i, int q) {
-  return ((size_t)(i >> 1) * kRec + q) * 2 + (i & 1);
+  return ((size_t)((i >> 6) * 32 + (i & 31)) * kRec + q) * 2 + ((i >> 5) & 1);
 }
 template <> __device__ __forceinline__ size_t xidx<double>(int i, int q) {
   return (size_t)i * kRec + q;
