@@ -264,7 +264,7 @@ fwh_status prepare_nt(fwh_handle h, int64_t nt) {
 int effective_cfg(const fwh_ctx *h, int64_t ntp) {
   const bool fp64 = h->precision == FWH_FP64;
   int cfg = h->cfg >= 0 ? h->cfg : default_cfg(h);
-  if (fwd_config(fp64, cfg).pipe == 1 && h->P * ntp >= ((int64_t)1 << 31)) {
+  if (fwd_config(fp64, cfg).pipe != 0 && h->P * ntp >= ((int64_t)1 << 31)) {
     for (int i = 0; i < fwd_num_configs(fp64); ++i)
       if (fwd_config(fp64, i).pipe == 0) return i;
   }
@@ -294,7 +294,7 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
   const bool fp64 = sizeof(T) == 8;
   const int cfg = effective_cfg(h, h->ntp);
   const FwdConfig c = fwd_config(fp64, cfg);
-  if (c.pipe == 1) {
+  if (c.pipe != 0) {
     fwh_status st0 = ensure_tmap(h, 32 * c.tk);
     if (st0 != FWH_OK) return st0;
   }
@@ -838,7 +838,7 @@ fwh_status batch_build(int n, const fwh_handle *hs, const void *const *fields,
     fwh_status st = plan(h, c, h0->side);
     if (st != FWH_OK) return fail(h0, st, h->err);
     CK(h0, cudaStreamSynchronize(h0->side));
-    if (c.pipe == 1) {
+    if (c.pipe != 0) {
       st = ensure_tmap(h, 32 * c.tk);
       if (st != FWH_OK) return fail(h0, st, h->err);
     }
@@ -1029,7 +1029,7 @@ fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, d
   CK(h, cudaMemcpyAsync(d_nv, nv.data(), nv.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   CK(h, cudaMemcpyAsync(d_sets, sets.data(), sets.size() * sizeof(int), cudaMemcpyHostToDevice,
                         s));
-  if (c.pipe == 1) {
+  if (c.pipe != 0) {
     alignas(64) unsigned char desc[128];
     if (!encode_x_tensor_map(desc, d_X, (unsigned long long)h->P * ntp, fp64, 32 * c.tk))
       return fail(h, FWH_ERR_CUDA, "cuTensorMapEncodeTiled refused the series layout");

@@ -51,6 +51,7 @@ namespace fwh {
 namespace {
 
 constexpr int kMaxObsPerWarp = 16;
+constexpr int kMaxObsPerWarpF32 = 9;  // the FP32 consumer unrolls its observer loop to this
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 template <typename T> struct Vec;
@@ -398,7 +399,32 @@ struct PipeState {
   unsigned stage_bytes, x_bytes;
   int nst;
   volatile int *abort;
+  int *released;  // in-line producer: per-stage count of warps done with it
+  int *issued;    // in-line producer: steps issued so far (for the drain)
 };
+
+// Threads per CTA: compute warps, plus the producer warp of the TMA pipeline
+// (pipe 1); the in-line producer (pipe 2) has none.
+template <int NW, int PIPE>
+constexpr int cta_threads() { return (NW + (PIPE == 1 ? 1 : 0)) * 32; }
+
+// In-line producer: load step j (in-item index) of `it` into stage `slot`.
+// Step j covers panel p_begin + j % np and chunk k_begin + (j / np) CH.
+template <typename T, int TK, int NW>
+__device__ __forceinline__ void issue_step(const FwdArgs<T> &a, const Item<T, NW> &it,
+                                           const PipeState &ps, int j, unsigned slot) {
+  constexpr int CH = 32 * TK;
+  const int np = it.p_end - it.p_begin;
+  const int p = it.p_begin + j % np;
+  const int k0 = it.k_begin + (j / np) * CH;
+  const unsigned cbytes = (unsigned)((it.o_end - it.o_begin) * kRec * sizeof(T));
+  uint64_t *bar = &ps.full[slot];
+  unsigned char *dst = ps.stage0 + (size_t)slot * ps.stage_bytes;
+  mbar_expect_tx(bar, ps.x_bytes + cbytes);
+  const int row = p * a.ntp + k0;  // tensor rows are 128 bytes
+  tma_load_2d(dst, a.tmX, 0, sizeof(T) == 4 ? row >> 1 : row, bar);
+  bulk_load(dst + ps.x_bytes, a.coef + ((size_t)p * a.O + it.o_begin) * kRec, cbytes, bar);
+}
 
 // Producer (one lane): stream the steps of one item into the stage ring, and
 // warm L2 with the rows and records kPrefetchSteps steps beyond the ring so
@@ -577,7 +603,7 @@ __device__ __forceinline__ void lds_coef(unsigned rec, Coef &k) {
   k.off = lds_s32_stage(rec + 4 * slot::off);
 }
 
-template <int TK, int NW, bool PF>
+template <int TK, int NW, bool PF, int PIPE>
 __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
                                                  const Item<float, NW> &it,
                                                  const PipeState &ps, unsigned &step,
@@ -599,8 +625,10 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
   const bool last = lane == 31;
   const unsigned first = lane == 0;
   unsigned s = step % (unsigned)ps.nst, ph = (step / (unsigned)ps.nst) & 1u;
+  const int nsteps = (it.p_end - it.p_begin) * ((it.k_end - it.k_begin) / CH);
+  int j = 0;  // in-item step index
   for (int k0 = it.k_begin; k0 < it.k_end; k0 += CH) {
-    for (int p = it.p_begin; p < it.p_end; ++p, ++step) {
+    for (int p = it.p_begin; p < it.p_end; ++p, ++step, ++j) {
       if (!mbar_wait(&ps.full[s], ph, a.err, ps.abort)) return;
       const unsigned stg = stage_token(stage0 + s * ps.stage_bytes);
       float X[NP][2][kRec];  // [pair row][sample s, s + 32][value]
@@ -620,7 +648,9 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
       // read each record right before its use.
       Coef k;
       if (PF && it.nobs > 0) lds_coef(crec, k);
-      for (int m = 0; m < it.nobs; ++m) {
+#pragma unroll
+      for (int m = 0; m < kMaxObsPerWarpF32; ++m) {
+        if (m >= it.nobs) break;
         if (!PF) lds_coef(crec + (unsigned)m * NW * RB, k);
         const unsigned w1 = win_s + (unsigned)m * win_b + (unsigned)k.off * 4u;
         float u[NP][2], v[NP][2];
@@ -663,7 +693,21 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
         if (PF && m + 1 < it.nobs) k = kn;
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&ps.empty[s]);
+      if constexpr (PIPE == 2) {
+        // the last warp done with this stage refills it with step j + nst
+        if (lane == 0) {
+          __threadfence_block();
+          const int done = atomicAdd(&ps.released[s], 1) + 1;
+          if (done % NW == 0 && j + ps.nst < nsteps) {
+            __threadfence_block();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue_step<float, TK, NW>(a, it, ps, j + ps.nst, s);
+            atomicMax(ps.issued, (int)step + ps.nst + 1);
+          }
+        }
+      } else {
+        if (lane == 0) mbar_arrive(&ps.empty[s]);
+      }
       if (++s == (unsigned)ps.nst) {
         s = 0;
         ph ^= 1u;
@@ -687,7 +731,9 @@ __device__ __forceinline__ void drain_copies(const PipeState &ps, unsigned step,
 template <typename T, int TK, int NW>
 __device__ __forceinline__ unsigned char *pipe_setup(unsigned char *raw, int obs_per_cta,
                                                      int nst, uint64_t *bars,
-                                                     volatile int *abort, PipeState &ps) {
+                                                     volatile int *abort, PipeState &ps,
+                                                     int *released = nullptr,
+                                                     int *issued = nullptr) {
   constexpr int CH = 32 * TK;
   const unsigned base = smem_u32(raw);
   unsigned char *al = raw + ((1024u - (base & 1023u)) & 1023u);
@@ -698,11 +744,15 @@ __device__ __forceinline__ unsigned char *pipe_setup(unsigned char *raw, int obs
   ps.full = bars;
   ps.empty = bars + nst;
   ps.abort = abort;
+  ps.released = released;
+  ps.issued = issued;
   if (threadIdx.x == 0) {
     for (int s = 0; s < nst; ++s) {
       mbar_init(&ps.full[s], 1);
       mbar_init(&ps.empty[s], NW);
+      if (released) released[s] = 0;
     }
+    if (issued) *issued = 0;
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -716,7 +766,9 @@ constexpr int kMaxStages = 8;
 // warps run 3 (TK = 4) or 2 (TK = 8) per SM, with 8 compute warps 2 or 1.
 template <int TK, int NW, int PIPE>
 struct MinBlocks {
-  static constexpr int v = !PIPE ? 1 : (NW <= 4 ? (TK <= 4 ? 3 : 2) : (TK <= 4 ? 2 : 1));
+  static constexpr int v = !PIPE ? 1
+                           : PIPE == 2 ? (NW <= 4 ? (TK <= 4 ? 4 : 2) : (TK <= 4 ? 2 : 1))
+                                       : (NW <= 4 ? (TK <= 4 ? 3 : 2) : (TK <= 4 ? 2 : 1));
 };
 
 template <typename T, int TK, int NW, int PIPE, int ACC>
@@ -725,6 +777,28 @@ __device__ __forceinline__ void forward_cta(const FwdArgs<T> &a, int nst) {
   __shared__ int st[NW * kMaxObsPerWarp];
   if constexpr (PIPE == 0) {
     process_item_direct<T, TK, NW>(a, blockIdx.x, reinterpret_cast<T *>(smem_raw), st);
+  } else if constexpr (PIPE == 2) {
+    static_assert(sizeof(T) == 4 && ACC >= 3, "the in-line producer serves the FP32 consumer");
+    __shared__ __align__(8) uint64_t bars[2 * kMaxStages];
+    __shared__ int released[kMaxStages];
+    __shared__ int issued;
+    __shared__ int abort_flag;
+    PipeState ps;
+    unsigned char *wbase = pipe_setup<T, TK, NW>(smem_raw, a.obs_per_cta, nst, bars,
+                                                 &abort_flag, ps, released, &issued);
+    const int w = threadIdx.x >> 5;
+    const Item<T, NW> it(a, blockIdx.x, w);
+    if (threadIdx.x == 0) {  // fill the ring
+      const int nsteps = (it.p_end - it.p_begin) * ((it.k_end - it.k_begin) / (32 * TK));
+      const int n0 = min(nst, nsteps);
+      for (int j = 0; j < n0; ++j) issue_step<T, TK, NW>(a, it, ps, j, (unsigned)j);
+      atomicMax(&issued, n0);
+    }
+    unsigned step = 0;
+    T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.win;
+    consume_item_f32<TK, NW, ACC == 4, 2>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
+    __syncthreads();
+    if (threadIdx.x == 0 && abort_flag) drain_copies(ps, (unsigned)issued, a.err);
   } else {
     __shared__ __align__(8) uint64_t bars[2 * kMaxStages];
     __shared__ int abort_flag;
@@ -743,7 +817,7 @@ __device__ __forceinline__ void forward_cta(const FwdArgs<T> &a, int nst) {
       const Item<T, NW> it(a, blockIdx.x, w);
       T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.win;
       if constexpr (ACC >= 3 && sizeof(T) == 4) {
-        consume_item_f32<TK, NW, ACC == 4>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
+        consume_item_f32<TK, NW, ACC == 4, 1>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
       } else {
         consume_item<T, TK, NW>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
       }
@@ -753,7 +827,7 @@ __device__ __forceinline__ void forward_cta(const FwdArgs<T> &a, int nst) {
 
 
 template <typename T, int TK, int NW, int PIPE, int ACC>
-__global__ void __launch_bounds__((NW + PIPE) * 32, (MinBlocks<TK, NW, PIPE>::v))
+__global__ void __launch_bounds__((cta_threads<NW, PIPE>()), (MinBlocks<TK, NW, PIPE>::v))
     k_forward(FwdArgs<T> a, int nst) {
   forward_cta<T, TK, NW, PIPE, ACC>(a, nst);
 }
@@ -774,12 +848,15 @@ __device__ __forceinline__ void forward_batch_cta(const FwdArgs<T> *args, const 
   __shared__ int s_item;
   __shared__ __align__(8) uint64_t bars[2 * kMaxStages];
   __shared__ int abort_flag;
+  __shared__ int released[kMaxStages];
+  __shared__ int issued;
   PipeState ps;
   unsigned char *wbase = smem_raw;
-  if constexpr (PIPE == 1) {
+  if constexpr (PIPE != 0) {
     int maxo = 0;
     for (int i = 0; i < n_surf; ++i) maxo = max(maxo, args[i].obs_per_cta);
-    wbase = pipe_setup<T, TK, NW>(smem_raw, maxo, nst, bars, &abort_flag, ps);
+    wbase = pipe_setup<T, TK, NW>(smem_raw, maxo, nst, bars, &abort_flag, ps,
+                                  PIPE == 2 ? released : nullptr, PIPE == 2 ? &issued : nullptr);
   }
   const int w = threadIdx.x >> 5;
   unsigned step = 0;
@@ -798,6 +875,18 @@ __device__ __forceinline__ void forward_batch_cta(const FwdArgs<T> *args, const 
     const int li = item - item_prefix[lo];
     if constexpr (PIPE == 0) {
       process_item_direct<T, TK, NW>(a, li, reinterpret_cast<T *>(smem_raw), st);
+    } else if constexpr (PIPE == 2) {
+      if (abort_flag) break;
+      const Item<T, NW> it(a, li, w);
+      if (threadIdx.x == 0) {  // fill the ring: every stage is free here
+        const int nsteps = (it.p_end - it.p_begin) * ((it.k_end - it.k_begin) / (32 * TK));
+        const int n0 = min(nst, nsteps);
+        for (int j = 0; j < n0; ++j)
+          issue_step<T, TK, NW>(a, it, ps, j, (step + (unsigned)j) % (unsigned)nst);
+        atomicMax(&issued, (int)step + n0);
+      }
+      T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.win;
+      consume_item_f32<TK, NW, ACC == 4, 2>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
     } else {
       if (abort_flag) break;
       if (w == NW) {
@@ -809,8 +898,8 @@ __device__ __forceinline__ void forward_batch_cta(const FwdArgs<T> *args, const 
         const Item<T, NW> it(a, li, w);
         T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.win;
         if constexpr (ACC >= 3 && sizeof(T) == 4) {
-          consume_item_f32<TK, NW, ACC == 4>(a, it, ps, step, wwin,
-                                               st + w * kMaxObsPerWarp);
+          consume_item_f32<TK, NW, ACC == 4, 1>(a, it, ps, step, wwin,
+                                                  st + w * kMaxObsPerWarp);
         } else {
           consume_item<T, TK, NW>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
         }
@@ -820,10 +909,14 @@ __device__ __forceinline__ void forward_batch_cta(const FwdArgs<T> *args, const 
   if constexpr (PIPE == 1) {
     if (w == NW && (threadIdx.x & 31) == 0) drain_copies(ps, step, args[0].err);
   }
+  if constexpr (PIPE == 2) {
+    __syncthreads();
+    if (threadIdx.x == 0 && abort_flag) drain_copies(ps, (unsigned)issued, args[0].err);
+  }
 }
 
 template <typename T, int TK, int NW, int PIPE, int ACC>
-__global__ void __launch_bounds__((NW + PIPE) * 32, (MinBlocks<TK, NW, PIPE>::v))
+__global__ void __launch_bounds__((cta_threads<NW, PIPE>()), (MinBlocks<TK, NW, PIPE>::v))
     k_forward_batch(const FwdArgs<T> *args, const int *item_prefix, int n_surf, int total,
                     int *counter, int nst) {
   forward_batch_cta<T, TK, NW, PIPE, ACC>(args, item_prefix, n_surf, total, counter, nst);
@@ -843,12 +936,19 @@ __global__ void __maxnreg__(200)
 // observer's record read ahead.  wide: register cap 200 instead of the launch
 // bounds' occupancy target.  Register use (ptxas, sm_103a): tk 4 shapes 126
 // to 128 (three CTAs of five warps per SM), tk 8 168 (two).
-const FwdConfig kCfgF32[] = {
+constexpr FwdConfig kCfgF32[] = {
     {1, 4, 4, 9, 224, 4, 3, 3, 0},
     {1, 4, 4, 9, 224, 4, 3, 4, 0},
-    {1, 4, 4, 8, 224, 4, 3, 3, 0},
+    {2, 4, 4, 9, 224, 4, 2, 3, 0},
+    {2, 4, 8, 9, 224, 4, 3, 3, 0},
     {1, 8, 4, 9, 352, 2, 3, 3, 0},
 };
+constexpr bool f32_obs_fit() {
+  for (const FwdConfig &c : kCfgF32)
+    if (c.obs_per_warp > kMaxObsPerWarpF32) return false;
+  return true;
+}
+static_assert(f32_obs_fit(), "an FP32 shape has more observers per warp than the unrolled loop");
 const FwdConfig kCfgF64[] = {
     {0, 2, 8, 16, 128, 8, 0, 0, 0},
     {1, 2, 8, 9, 128, 8, 3, 0, 0},
@@ -876,7 +976,7 @@ cudaError_t launch_one(const FwdArgs<T> &a, const FwdConfig &c, cudaStream_t s) 
   if (e != cudaSuccess) return e;
   const int items = a.nsets * a.n_obs_groups * a.n_segs;
   if (items <= 0) return cudaSuccess;
-  kern<<<items, (NW + PIPE) * 32, smem, s>>>(a, c.stages);
+  kern<<<items, cta_threads<NW, PIPE>(), smem, s>>>(a, c.stages);
   return cudaGetLastError();
 }
 
@@ -889,7 +989,8 @@ cudaError_t launch_batch_one(const FwdArgs<T> *d_args, const int *d_prefix, int 
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<n_ctas, (NW + PIPE) * 32, smem, s>>>(d_args, d_prefix, n_surf, total, d_counter, nst);
+  kern<<<n_ctas, cta_threads<NW, PIPE>(), smem, s>>>(d_args, d_prefix, n_surf, total, d_counter,
+                                                      nst);
   return cudaGetLastError();
 }
 
@@ -943,6 +1044,8 @@ bool encode_x_tensor_map(void *out128, const void *X, unsigned long long rows, b
 #define FWH_DISPATCH(T, c, CALL)                                                        \
   do {                                                                                   \
     if constexpr (sizeof(T) == 4) {                                                      \
+      if (c.pipe == 2 && c.tk == 4 && c.warps == 4 && c.acc == 3) return CALL(T, 4, 4, 2, 3); \
+      if (c.pipe == 2 && c.tk == 4 && c.warps == 8 && c.acc == 3) return CALL(T, 4, 8, 2, 3); \
       if (c.pipe == 1 && c.tk == 4 && c.warps == 4 && c.acc == 3) return CALL(T, 4, 4, 1, 3); \
       if (c.pipe == 1 && c.tk == 4 && c.warps == 4 && c.acc == 4) return CALL(T, 4, 4, 1, 4); \
       if (c.pipe == 1 && c.tk == 8 && c.warps == 4 && c.acc == 3) return CALL(T, 8, 4, 1, 3); \

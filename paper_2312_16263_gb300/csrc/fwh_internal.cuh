@@ -123,7 +123,8 @@ cudaError_t launch_adjoint(const AdjArgs<T> &a, cudaStream_t s);
 
 // Forward tile configurations (index into a table in fwh_forward.cu).
 struct FwdConfig {
-  int pipe;           // 0: direct loads, 1: TMA + mbarrier pipeline (producer warp)
+  int pipe;           // 0: direct loads, 1: TMA + mbarrier pipeline (producer warp),
+                      // 2: TMA pipeline refilled by the last warp done with a stage
   int tk;             // source samples per lane per chunk (chunk = 32 tk)
   int warps;          // compute warps per CTA
   int obs_per_warp;   // max observers per warp
