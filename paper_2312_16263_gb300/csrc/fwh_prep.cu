@@ -10,17 +10,18 @@
 // signal sum_s c_s F_s has moments sum_s c_s m(F_s) by linearity, so the
 // moments are computed once per panel instead of once per (panel, observer).
 //
-// The moments solve, on a window of the chunk plus a halo of H samples on
-// each side (clipped to the record), the tridiagonal system
+// FP64 (k_prep): the moments solve, on a window of the chunk plus a halo of H
+// samples on each side (clipped to the record), the tridiagonal system
 //   m_{j-1} + 4 m_j + m_{j+1} = 6 (F_{j+1} - 2 F_j + F_{j-1}) / dt^2
 // with m = 0 at the window ends: at the record ends this is the natural end
 // condition itself; at an artificial end the error decays as (2 - sqrt 3)^H
-// into the chunk, below the arithmetic's rounding for the chosen H.
+// into the chunk, below the arithmetic's rounding for the chosen H.  A CTA is
+// 16 panels x 8 series, one thread per (panel, series), sequential over the
+// window in source time; the forward elimination's values for the chunk and
+// right halo wait in shared memory for the back substitution.
 //
-// Thread mapping: a CTA is 16 panels x 8 series, one thread per
-// (panel, series), sequential over the window in source time; the forward
-// elimination's values for the chunk and right halo wait in shared memory
-// for the back substitution (interleaved by thread: conflict-free).
+// FP32 (k_prep_iir): the same moments by two first-order recursive filters
+// per 32-sample block (see the kernel), written as whole X tiles.
 #include "fwh_internal.cuh"
 
 namespace fwh {
@@ -69,7 +70,6 @@ template <> struct PrepChunk<double> { static constexpr int v = 64; };
 // Forward-prep tile: lanes map to panels for coalesced field loads (128 bytes
 // of one field component per warp-row), then to (panel, series) pairs.
 template <typename T> struct PrepTile;
-template <> struct PrepTile<float> { static constexpr int panels = 32, chunk = 128; };
 template <> struct PrepTile<double> { static constexpr int panels = 16, chunk = 64; };
 
 // Integrand `which` (0: Qn, 1..3: L_c) of panel po at sample i.
@@ -90,15 +90,9 @@ struct Integrand {
   }
 };
 
-// Element (sample i, value q) of a panel's X rows.  FP32 rows pair the
-// samples j and j + 32 of each 64-sample block: row 32 (i / 64) + i % 32
-// holds [q][(i / 32) & 1], so one 16-byte load yields the same two values of
-// both samples (the packed FP32x2 operands of the forward kernel); FP64 rows
-// are plain [i][q].
+// Element (sample i, value q) of a panel's FP64 X rows, plain [i][q].  (The
+// FP32 rows, which pair samples 32 apart, are written by k_prep_iir.)
 template <typename T> __device__ __forceinline__ size_t xidx(int i, int q);
-template <> __device__ __forceinline__ size_t xidx<float>(int i, int q) {
-  return ((size_t)((i >> 6) * 32 + (i & 31)) * kRec + q) * 2 + ((i >> 5) & 1);
-}
 template <> __device__ __forceinline__ size_t xidx<double>(int i, int q) {
   return (size_t)i * kRec + q;
 }
@@ -262,6 +256,184 @@ __global__ void __launch_bounds__(PrepTile<T>::panels * 8) k_prep(PrepArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------
+// FP32 forward prep by recursive filtering.  The natural-spline moments of a
+// record F_0..F_{N-1} solve tridiag(1, 4, 1) m = r on rows 1..N-2 with
+// m_0 = m_{N-1} = 0, r_k = 6 (F_{k+1} - 2 F_k + F_{k-1}) / dt^2.  Extending r
+// odd-periodically (r_0 = r_{N-1} = 0, r_{-k} = -r_k, period 2 (N - 1)) makes
+// the end conditions hold by symmetry, so m is the infinite Toeplitz inverse
+// applied to the extended r.  That inverse factors as
+//   m = -rho (1 - rho z)^-1 (1 - rho z^-1)^-1 r,   rho = sqrt(3) - 2,
+// a causal recursion y_k = r_k + rho y_{k-1} followed by an anti-causal one
+// x_k = y_k + rho x_{k+1}, m_k = -rho x_k.  Each thread filters 32 samples,
+// starting both recursions H samples outside its block (error |rho|^H, below
+// FP32 rounding for H = 16), so every sample block is independent: no
+// sequential sweep over the window, no intermediate values in HBM.
+//
+// CTA tile: 16 panels x 64 samples (one 64-sample block of the FP32 rows);
+// thread (half, panel, series) filters samples [32 half, 32 half + 32) of the
+// tile.  Phase A stages the four integrands of the rows the filters reach
+// (folded back into the record), phase B filters into a shared copy of the
+// tile in the row layout of X, phase C writes the tile with coalesced 16-byte
+// stores (4 KB contiguous per panel).
+// ---------------------------------------------------------------------------
+constexpr int kIirPanels = 16;
+constexpr int kIirChunk = 64;
+constexpr int kIirJ = 32;
+constexpr int kIirThreads = kIirPanels * 8 * (kIirChunk / kIirJ);
+constexpr int kIirH = Prec<float>::halo;
+constexpr int kIirRows = kIirChunk + 2 * kIirH + 6;  // bound on the staged rows
+constexpr int kIirQ = 20;                            // integrand stride in a staged row
+constexpr int kIirRow = 4 * kIirQ;                   // staged row stride (floats)
+
+__global__ void __launch_bounds__(kIirThreads, 2) k_prep_iir(PrepArgs<float> a) {
+  constexpr int NP = kIirPanels, H = kIirH, J = kIirJ;
+  constexpr float rho = -0.267949192431122706f;  // sqrt(3) - 2
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // tile [NP][32 rows][16][2] (16-byte chunk index of odd panels XOR 4, so
+  // that the four panels of a warp spread over the banks), then the staged
+  // integrands [rows][4 (stride kIirQ)][NP]
+  float *tile = reinterpret_cast<float *>(smem_raw);
+  float *sb = tile + NP * kIirChunk * kRec;
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * kIirChunk;
+  const int p0 = blockIdx.y * NP;
+  const int N = a.nt;
+  if (c0 < N) {
+    // staged integrand rows: the tile's filter reach plus FD neighbours, and
+    // for a tile at the record end the rows its window folds back onto
+    const int reach_lo = c0 - H - 3, reach_hi = c0 + kIirChunk + H + 3;
+    const int lo = max(0, min(reach_lo, 2 * (N - 1) - reach_hi));
+    const int hi = min(N, reach_hi);
+    // ---- phase A: integrands ----------------------------------------------
+    {
+      const int pl = tid % NP;
+      const int p = p0 + pl;
+      const bool live = p < a.P;
+      const int po = live ? (a.perm ? a.perm[p] : p) : 0;
+      float n0 = 0.f, n1 = 0.f, n2 = 0.f, Un = 0.f;
+      if (live) {
+        n0 = (float)a.n[3 * p];
+        n1 = (float)a.n[3 * p + 1];
+        n2 = (float)a.n[3 * p + 2];
+        Un = (float)(a.ca * a.n[3 * p] + a.sa * a.n[3 * p + 1]);
+      }
+      // all field loads of this thread's rows first, then the integrands
+      constexpr int RS = kIirThreads / NP;               // row stride between passes
+      constexpr int RPT = (kIirRows + RS - 1) / RS;      // passes
+      float fv[RPT][5];
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        const int i = lo + tid / NP + u * RS;
+        const bool ok = live && i < hi;
+        const float *b = a.fields + (size_t)(ok ? i : 0) * 5 * a.P + po;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) fv[u][c] = ok ? b[(size_t)c * a.P] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        const int i = lo + tid / NP + u * RS;
+        if (i >= hi) break;
+        const float rho_ = fv[u][0], u0 = fv[u][1], u1 = fv[u][2], u2 = fv[u][3], pp = fv[u][4];
+        const float un = u0 * n0 + u1 * n1 + u2 * n2;
+        const float r1 = 1.f + rho_;
+        const float utn = Un + un;
+        float *row = sb + (size_t)(i - lo) * kIirRow + pl;
+        row[0] = rho_ * Un + r1 * un;                // Qn   (Eq. Qn_New_nd)
+        row[kIirQ] = pp * n0 + r1 * u0 * utn;        // L_1  (Eq. Li_New_nd)
+        row[2 * kIirQ] = pp * n1 + r1 * u1 * utn;
+        row[3 * kIirQ] = pp * n2 + r1 * u2 * utn;
+      }
+    }
+    __syncthreads();
+    // ---- phase B: series and moments ----------------------------------------
+    const int s = tid & 7;
+    const int pl = (tid >> 3) % NP;
+    const int h = tid / (8 * NP);
+    const int ks = c0 + J * h;
+    const bool deriv = (s == 0) || (s >= 2 && s <= 4);
+    const int qi = (s <= 1) ? 0 : 1 + (s - 2) % 3;
+    const float *col = sb + qi * kIirQ + pl - (size_t)lo * kIirRow;  // B(i) = col[i * kIirRow]
+    const float inv2h = (float)(0.5 / a.dt);
+    const float s6 = (float)(6.0 / (a.dt * a.dt));
+    // interior series sample F_i = fa B(i+1) + fb B(i) + fc B(i-1)
+    const float fa = deriv ? inv2h : 0.f, fb = deriv ? 0.f : 1.f, fc = -fa;
+    auto B = [&](int i) -> float { return col[(size_t)i * kIirRow]; };
+    float *tp = tile + (size_t)pl * kIirChunk * kRec;
+    const int swz = (pl & 1) << 4;
+    auto put = [&](int t, int q, float v) { tp[(((t * kRec + q) * 2) + h) ^ swz] = v; };
+    float y[J + H];
+    const bool interior = ks - H - 1 >= 1 && ks + J + H <= N - 2;
+    if (interior) {
+      int k = ks - H;
+      float Bk = B(k), Bk1 = B(k + 1);
+      const float Bkm = B(k - 1);
+      float Fm = fa * Bk + fb * Bkm + fc * B(k - 2);   // F_{k-1}
+      float F0 = fa * Bk1 + fb * Bk + fc * Bkm;        // F_k
+      float yy = 0.f;
+#pragma unroll
+      for (int t = 0; t < J + 2 * H; ++t, ++k) {
+        const float Bk2 = B(k + 2);
+        const float Fp = fa * Bk2 + fb * Bk1 + fc * Bk;  // F_{k+1}
+        yy = s6 * (Fp - 2.f * F0 + Fm) + rho * yy;
+        if (t >= H) y[t - H] = yy;
+        if (t >= H && t < H + J) put(t - H, s, F0);
+        Bk = Bk1;
+        Bk1 = Bk2;
+        Fm = F0;
+        F0 = Fp;
+      }
+    } else {
+      // record ends: one-sided derivatives at the first and last frame, and r
+      // on the odd-periodic extension
+      auto F = [&](int i) -> float {
+        if (!deriv) return B(i);
+        if (i == 0) return (-3.f * B(0) + 4.f * B(1) - B(2)) * inv2h;
+        if (i == N - 1) return (3.f * B(N - 1) - 4.f * B(N - 2) + B(N - 3)) * inv2h;
+        return (B(i + 1) - B(i - 1)) * inv2h;
+      };
+      const int L2 = 2 * (N - 1);
+      auto r_at = [&](int kk) -> float {
+        int km = kk % L2;
+        if (km < 0) km += L2;
+        float sg = 1.f;
+        if (km >= N - 1) {
+          km = L2 - km;
+          sg = -1.f;
+        }
+        if (km == 0 || km == N - 1) return 0.f;
+        return sg * s6 * (F(km + 1) - 2.f * F(km) + F(km - 1));
+      };
+      float yy = 0.f;
+#pragma unroll
+      for (int t = 0; t < J + 2 * H; ++t) {
+        yy = r_at(ks - H + t) + rho * yy;
+        if (t >= H) y[t - H] = yy;
+      }
+#pragma unroll
+      for (int t = 0; t < J; ++t) put(t, s, ks + t < N ? F(ks + t) : 0.f);
+    }
+    float xx = 0.f;
+#pragma unroll
+    for (int t = J + H - 1; t >= 0; --t) {
+      xx = y[t] + rho * xx;
+      if (t < J) put(t, 8 + s, ks + t < N ? -rho * xx : 0.f);
+    }
+  } else {
+    for (int idx = tid; idx < NP * kIirChunk * kRec; idx += kIirThreads) tile[idx] = 0.f;
+  }
+  __syncthreads();
+  // ---- phase C: tile -> X (16-byte chunks, un-swizzled) ------------------------
+  constexpr int V4 = kIirChunk * kRec / 4;  // float4 per panel
+  for (int idx = tid; idx < NP * V4; idx += kIirThreads) {
+    const int pl = idx / V4, v = idx % V4;
+    const int p = p0 + pl;
+    if (p < a.P)
+      reinterpret_cast<float4 *>(a.X + ((size_t)p * a.ntp + c0) * kRec)[v] =
+          reinterpret_cast<const float4 *>(tile)[pl * V4 + (v ^ ((pl & 1) << 2))];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Adjoint of k_prep followed by the Jacobian of the integrands.
 // Xbar[p][i][s] = dLoss/dF_s(i), Xbar[p][i][8+s] = dLoss/dm_s(i).  For each
 // series: G_s = Xbar_s + (6/dt^2) D2^T T^{-1} mbar (transpose of the moment
@@ -379,19 +551,33 @@ __global__ void __launch_bounds__(kThreads) k_prep_adj(PrepAdjArgs<T> a) {
 
 template <typename T>
 cudaError_t launch_prep(const PrepArgs<T> &a0, cudaStream_t s) {
-  constexpr int NP = PrepTile<T>::panels;
-  constexpr int H = Prec<T>::halo;
-  PrepArgs<T> a = a0;
-  a.chunk = PrepTile<T>::chunk;
-  // integrand rows (chunk + 2 halos + 2 FD neighbours) x 4 x NP, plus the
-  // right-halo elimination values H x (NP * 8)
-  const size_t smem = ((size_t)(a.chunk + 2 * H + 2) * 4 * NP + (size_t)H * NP * 8) * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(k_prep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid((a.P + NP - 1) / NP, (a.ntp + a.chunk - 1) / a.chunk);
-  k_prep<T><<<grid, NP * 8, smem, s>>>(a);
-  return cudaGetLastError();
+  if constexpr (sizeof(T) == 4) {
+    // tile + staged integrand rows
+    const size_t smem =
+        ((size_t)kIirPanels * kIirChunk * kRec + (size_t)kIirRows * kIirRow) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_prep_iir, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    if (a0.ntp % kIirChunk != 0) return cudaErrorInvalidValue;
+    dim3 grid(a0.ntp / kIirChunk, (a0.P + kIirPanels - 1) / kIirPanels);
+    k_prep_iir<<<grid, kIirThreads, smem, s>>>(a0);
+    return cudaGetLastError();
+  } else {
+    constexpr int NP = PrepTile<T>::panels;
+    constexpr int H = Prec<T>::halo;
+    PrepArgs<T> a = a0;
+    a.chunk = PrepTile<T>::chunk;
+    // integrand rows (chunk + 2 halos + 2 FD neighbours) x 4 x NP, plus the
+    // right-halo elimination values H x (NP * 8)
+    const size_t smem =
+        ((size_t)(a.chunk + 2 * H + 2) * 4 * NP + (size_t)H * NP * 8) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(k_prep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.P + NP - 1) / NP, (a.ntp + a.chunk - 1) / a.chunk);
+    k_prep<T><<<grid, NP * 8, smem, s>>>(a);
+    return cudaGetLastError();
+  }
 }
 
 template <typename T>
