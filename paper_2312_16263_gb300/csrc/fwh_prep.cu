@@ -276,16 +276,16 @@ __global__ void __launch_bounds__(PrepTile<T>::panels * 8) k_prep(PrepArgs<T> a)
 // tile in the row layout of X, phase C writes the tile with coalesced 16-byte
 // stores (4 KB contiguous per panel).
 // ---------------------------------------------------------------------------
-constexpr int kIirPanels = 16;
+constexpr int kIirPanels = 8;
 constexpr int kIirChunk = 64;
 constexpr int kIirJ = 32;
 constexpr int kIirThreads = kIirPanels * 8 * (kIirChunk / kIirJ);
 constexpr int kIirH = Prec<float>::halo;
 constexpr int kIirRows = kIirChunk + 2 * kIirH + 6;  // bound on the staged rows
-constexpr int kIirQ = 20;                            // integrand stride in a staged row
+constexpr int kIirQ = 8;  // integrand stride in a staged row (4 integrands x 4 panels of a warp: distinct banks)
 constexpr int kIirRow = 4 * kIirQ;                   // staged row stride (floats)
 
-__global__ void __launch_bounds__(kIirThreads, 2) k_prep_iir(PrepArgs<float> a) {
+__global__ void __launch_bounds__(kIirThreads, 4) k_prep_iir(PrepArgs<float> a) {
   constexpr int NP = kIirPanels, H = kIirH, J = kIirJ;
   constexpr float rho = -0.267949192431122706f;  // sqrt(3) - 2
   extern __shared__ __align__(16) unsigned char smem_raw[];
