@@ -361,9 +361,9 @@ __global__ void __launch_bounds__(kIirThreads, 4) k_prep_iir(PrepArgs<float> a) 
     float *tp = tile + (size_t)pl * kIirChunk * kRec;
     const int swz = (pl & 1) << 4;
     auto put = [&](int t, int q, float v) { tp[(((t * kRec + q) * 2) + h) ^ swz] = v; };
-    float y[J + H];
     const bool interior = ks - H - 1 >= 1 && ks + J + H <= N - 2;
     if (interior) {
+      float y[J + H];
       int k = ks - H;
       float Bk = B(k), Bk1 = B(k + 1);
       const float Bkm = B(k - 1);
@@ -382,9 +382,15 @@ __global__ void __launch_bounds__(kIirThreads, 4) k_prep_iir(PrepArgs<float> a) 
         Fm = F0;
         F0 = Fp;
       }
+      float xx = 0.f;
+#pragma unroll
+      for (int t = J + H - 1; t >= 0; --t) {
+        xx = y[t] + rho * xx;
+        if (t < J) put(t, 8 + s, -rho * xx);
+      }
     } else {
-      // record ends: one-sided derivatives at the first and last frame, and r
-      // on the odd-periodic extension
+      // record ends (few tiles, compact code): one-sided derivatives at the
+      // first and last frame, r on the odd-periodic extension
       auto F = [&](int i) -> float {
         if (!deriv) return B(i);
         if (i == 0) return (-3.f * B(0) + 4.f * B(1) - B(2)) * inv2h;
@@ -403,20 +409,21 @@ __global__ void __launch_bounds__(kIirThreads, 4) k_prep_iir(PrepArgs<float> a) 
         if (km == 0 || km == N - 1) return 0.f;
         return sg * s6 * (F(km + 1) - 2.f * F(km) + F(km - 1));
       };
+      float ye[J + H];
       float yy = 0.f;
-#pragma unroll
+#pragma unroll 1
       for (int t = 0; t < J + 2 * H; ++t) {
         yy = r_at(ks - H + t) + rho * yy;
-        if (t >= H) y[t - H] = yy;
+        if (t >= H) ye[t - H] = yy;
       }
-#pragma unroll
+#pragma unroll 1
       for (int t = 0; t < J; ++t) put(t, s, ks + t < N ? F(ks + t) : 0.f);
-    }
-    float xx = 0.f;
-#pragma unroll
-    for (int t = J + H - 1; t >= 0; --t) {
-      xx = y[t] + rho * xx;
-      if (t < J) put(t, 8 + s, ks + t < N ? -rho * xx : 0.f);
+      float xx = 0.f;
+#pragma unroll 1
+      for (int t = J + H - 1; t >= 0; --t) {
+        xx = ye[t] + rho * xx;
+        if (t < J) put(t, 8 + s, ks + t < N ? -rho * xx : 0.f);
+      }
     }
   } else {
     for (int idx = tid; idx < NP * kIirChunk * kRec; idx += kIirThreads) tile[idx] = 0.f;
