@@ -873,7 +873,9 @@ fwh_status batch_build(int n, const fwh_handle *hs, const void *const *fields,
   int dev = 0, sms = 0;
   CK(h0, cudaGetDevice(&dev));
   CK(h0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  bp.ctas = std::max(1, std::min(bp.total, sms * 2));
+  int per_sm = 0;
+  CK(h0, forward_batch_occupancy<T>(cfg, &per_sm));
+  bp.ctas = std::max(1, std::min(bp.total, sms * std::max(1, per_sm)));
   return FWH_OK;
 }
 

@@ -1079,6 +1079,31 @@ cudaError_t launch_forward_batch(const FwdArgs<T> *d_args, const int *d_prefix, 
 #undef FWH_CALL_BATCH
 }
 
+// Resident CTAs per SM of the persistent kernel for a config.
+template <typename T, int TK, int NW, int PIPE, int ACC>
+cudaError_t batch_occupancy_one(const FwdConfig &c, size_t smem, int *per_sm) {
+  auto kern = c.wide ? k_forward_batch_wide<T, TK, NW, PIPE, ACC>
+                     : k_forward_batch<T, TK, NW, PIPE, ACC>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, cta_threads<NW, PIPE>(),
+                                                       smem);
+}
+
+template <typename T>
+cudaError_t forward_batch_occupancy(int cfg, int *per_sm) {
+  const FwdConfig c = fwd_config(sizeof(T) == 8, cfg);
+  const size_t smem = smem_for<T>(c, c.warps * c.obs_per_warp);
+  *per_sm = 0;
+#define FWH_CALL_OCC(TT, TK, NW, PIPE, ACC) batch_occupancy_one<TT, TK, NW, PIPE, ACC>(c, smem, per_sm)
+  FWH_DISPATCH(T, c, FWH_CALL_OCC);
+#undef FWH_CALL_OCC
+}
+
+template cudaError_t forward_batch_occupancy<float>(int, int *);
+template cudaError_t forward_batch_occupancy<double>(int, int *);
+
 template <typename T>
 cudaError_t launch_plan(T *coef, const int *set_begin, int nsets, int O, int slack,
                         int *i0max_tab, int *err, cudaStream_t s) {

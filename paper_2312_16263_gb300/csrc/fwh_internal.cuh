@@ -137,6 +137,9 @@ struct FwdConfig {
 };
 // Bytes of dynamic shared memory a config needs for `obs_per_cta` observers.
 size_t fwd_smem_bytes(bool fp64, const FwdConfig &c, int obs_per_cta);
+// CTAs of the persistent batch kernel that fit on one SM for config `cfg`.
+template <typename T>
+cudaError_t forward_batch_occupancy(int cfg, int *per_sm);
 // Encode the TMA descriptor of X ([rows][16] elements of 4 or 8 bytes) into a
 // host buffer of 128 bytes; returns false if the driver refuses.
 bool encode_x_tensor_map(void *out128, const void *X, unsigned long long rows, bool fp64,

@@ -1,0 +1,97 @@
+"""The N > 1 path of bench.py on CPU ranks (gloo, world size 2).
+
+Observers are independent, so ranks shard the observer set and need no
+collective on the data path: each rank owns an equally sized, distinct set,
+the timing is reduced with a max over ranks, and rank 0 alone prints.  Here
+the per-rank work is the CPU oracle (no GPU on this machine), which checks
+that the shards together give exactly the unsharded result.
+"""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+@pytest.mark.parametrize("ws", [2, 4])
+def test_rank_observer_sets_are_distinct_and_equal(ws):
+    import bench
+    sets = [bench.rank_workload(r, ws).observers for r in range(ws)]
+    base = bench.rank_workload(0, ws)
+    for r in range(ws):
+        w = bench.rank_workload(r, ws)
+        assert w.observers.shape == base.observers.shape
+        assert w.surface.n_panels == base.surface.n_panels and w.nt == base.nt
+    allobs = np.concatenate(sets)
+    d = np.linalg.norm(allobs[:, None, :] - allobs[None, :, :], axis=-1)
+    np.fill_diagonal(d, np.inf)
+    assert d.min() > 1e-6          # no observer is computed twice
+
+
+def _worker(rank, ws, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    import bench
+    from fwh_inputs import workload
+    from oracle import Oracle
+    wsz, rk, _ = bench.dist_setup()
+    assert (wsz, rk) == (ws, rank)
+    assert bench.max_over_ranks(float(rank + 1), ws) == float(ws)
+    w = workload(1, scale=0.25)
+    mine = np.arange(rank, w.observers.shape[0], ws)     # this rank's observer shard
+    f = w.fields("float64").numpy()
+    p, ts, nv = Oracle.from_workload(w).forward(f, w.observers[mine])
+    # the test gathers the shards to compare them; the timed path never does
+    gathered = [None] * ws
+    dist.all_gather_object(gathered, (mine.tolist(), p.tolist(), nv.tolist()))
+    bench.barrier(ws)
+    if rank == 0:
+        with open(os.path.join(out_dir, "shards.json"), "w") as fh:
+            json.dump(gathered, fh)
+    dist.destroy_process_group()
+
+
+def test_gloo_two_ranks_shards_reassemble_the_unsharded_result(tmp_path):
+    from fwh_inputs import workload
+    from oracle import Oracle
+    ws = 2
+    mp.start_processes(_worker, args=(ws, _free_port(), str(tmp_path)), nprocs=ws,
+                       start_method="spawn")
+    shards = json.load(open(tmp_path / "shards.json"))
+    w = workload(1, scale=0.25)
+    p_all, _, nv_all = Oracle.from_workload(w).forward(w.fields("float64").numpy(),
+                                                        w.observers)
+    seen = []
+    for idx, p, nv in shards:
+        np.testing.assert_array_equal(np.asarray(p), p_all[idx])
+        np.testing.assert_array_equal(np.asarray(nv), nv_all[idx])
+        seen += idx
+    assert sorted(seen) == list(range(w.observers.shape[0]))
+
+
+def test_reference_arm_under_torchrun_prints_once(tmp_path):
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+           "--steps", "1", "--warmup", "0"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["n_gpus"] == 2
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
