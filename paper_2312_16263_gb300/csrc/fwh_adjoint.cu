@@ -30,43 +30,77 @@ __global__ void k_grad_pad(const double *grad_p, const int *n_valid, T *Gt, int 
     Gt[(size_t)o * ntp + j] = (j < nv && j < nt) ? (T)grad_p[(size_t)o * nt + j] : T(0);
 }
 
+// One CTA per (panel, group of 8 chunks), one warp per chunk.  The panel's
+// records are staged in shared memory in tiles of kObsTile observers (read
+// back as broadcasts), and each lane loads the two gradient bins of the next
+// observer while it accumulates the current one.
+constexpr int kObsTile = 128;
+
 template <typename T, int TK>
 __global__ void __launch_bounds__(256) k_adjoint(const T *coef, const T *Gt, T *Xbar, int P,
                                                  int O, int ntp) {
   constexpr int CH = 32 * TK;
+  __shared__ __align__(16) T srec[kObsTile * kRec];
   const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int w = threadIdx.x >> 5;
   const int nch = ntp / CH;
-  const int p = gw / nch;
-  if (p >= P) return;
-  const int k0 = (gw % nch) * CH;
+  const int ngrp = (nch + 7) / 8;
+  const int p = blockIdx.x / ngrp;
+  const int ch = (blockIdx.x % ngrp) * 8 + w;
+  const bool live = ch < nch;  // warps past the last chunk only help staging
+  const int k0 = ch * CH;
   T acc[TK][kRec];
 #pragma unroll
   for (int j = 0; j < TK; ++j)
 #pragma unroll
     for (int s = 0; s < kRec; ++s) acc[j][s] = T(0);
   const T *rec0 = coef + (size_t)p * O * kRec;
-  for (int o = 0; o < O; ++o) {
-    const T *rec = rec0 + (size_t)o * kRec;
-    T c[12];
+  for (int ob = 0; ob < O; ob += kObsTile) {
+    const int no = min(kObsTile, O - ob);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < no * kRec; idx += blockDim.x)
+      srec[idx] = rec0[(size_t)ob * kRec + idx];
+    __syncthreads();
+    if (!live) continue;
+    auto bins = [&](int o, T (&g0)[TK], T (&g1)[TK]) {
+      const int i0 = i0_of<T>(srec[o * kRec + slot::i0]);
+      const T *G = Gt + (size_t)(ob + o) * ntp;
 #pragma unroll
-    for (int s = 0; s < 12; ++s) c[s] = __ldg(rec + s);  // c0..c7, a, b, cc, dd
-    const int i0 = i0_of<T>(__ldg(rec + slot::i0));
-    const T *G = Gt + (size_t)o * ntp;
+      for (int j = 0; j < TK; ++j) {
+        const int jb = k0 + lane + 32 * j - i0;  // bin fed by the left spline node
+        g0[j] = jb >= 0 ? __ldg(G + jb) : T(0);
+        g1[j] = jb >= 1 ? __ldg(G + jb - 1) : T(0);
+      }
+    };
+    T g0[TK], g1[TK];
+    bins(0, g0, g1);
+    for (int o = 0; o < no; ++o) {
+      T n0[TK], n1[TK];
+      if (o + 1 < no) bins(o + 1, n0, n1);
+      const T *r = srec + o * kRec;
+      T c[12];
 #pragma unroll
-    for (int j = 0; j < TK; ++j) {
-      const int jb = k0 + lane + 32 * j - i0;  // bin fed by the left spline node
-      const T g0 = jb >= 0 ? __ldg(G + jb) : T(0);
-      const T g1 = jb >= 1 ? __ldg(G + jb - 1) : T(0);
-      const T gF = c[8] * g0 + c[9] * g1;
-      const T gM = c[10] * g0 + c[11] * g1;
+      for (int s = 0; s < 12; ++s) c[s] = r[s];  // c0..c7, then the four weights
 #pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        acc[j][s] = fma(c[s], gF, acc[j][s]);
-        acc[j][8 + s] = fma(c[s], gM, acc[j][8 + s]);
+      for (int j = 0; j < TK; ++j) {
+        const T gF = c[slot::a] * g0[j] + c[slot::b] * g1[j];
+        const T gM = c[slot::cc] * g0[j] + c[slot::dd] * g1[j];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          acc[j][s] = fma(c[slot::c + s], gF, acc[j][s]);
+          acc[j][8 + s] = fma(c[slot::c + s], gM, acc[j][8 + s]);
+        }
+      }
+      if (o + 1 < no) {
+#pragma unroll
+        for (int j = 0; j < TK; ++j) {
+          g0[j] = n0[j];
+          g1[j] = n1[j];
+        }
       }
     }
   }
+  if (!live) return;
   T *out = Xbar + ((size_t)p * ntp + k0 + lane) * kRec;
 #pragma unroll
   for (int j = 0; j < TK; ++j)
@@ -85,9 +119,9 @@ cudaError_t launch_adjoint(const AdjArgs<T> &a, cudaStream_t s) {
   k_grad_pad<T><<<gg, 256, 0, s>>>(a.grad_p, a.n_valid, Gt, a.O, a.nt, a.ntp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const long warps = (long)a.P * (a.ntp / CH);
-  const int blocks = (int)((warps + 7) / 8);
-  k_adjoint<T, TK><<<blocks, 256, 0, s>>>(a.coef, Gt, a.Xbar, a.P, a.O, a.ntp);
+  const long blocks = (long)a.P * ((a.ntp / CH + 7) / 8);
+  if (blocks <= 0) return cudaSuccess;
+  k_adjoint<T, TK><<<(unsigned)blocks, 256, 0, s>>>(a.coef, Gt, a.Xbar, a.P, a.O, a.ntp);
   return cudaGetLastError();
 }
 
