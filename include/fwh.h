@@ -175,7 +175,7 @@ fwh_status fwh_check(fwh_handle h, void *stream);
  * (FWH_ERR_ARG otherwise: there is no staging).
  * Scratch: the prepared series and per-call tables live in one file-scope
  * device array of 64 MiB that every GPU loading the library reserves until
- * the process exits; a problem needing more (about P x round_up(nt, 128) x
+ * the process exits; a problem needing more (about P x round_up(nt, 256) x
  * 64 bytes for FWH_MIXED, x 128 for FWH_FP64) is rejected with FWH_ERR_ARG
  * and a message giving both sizes.  The first call on each device looks up
  * the array's device address (cudaGetSymbolAddress) with that device
