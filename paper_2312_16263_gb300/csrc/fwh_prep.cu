@@ -554,6 +554,166 @@ __global__ void __launch_bounds__(kThreads) k_prep_adj(PrepAdjArgs<T> a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 adjoint of k_prep_iir followed by the integrand Jacobian.  With
+// m = A r, r = (6/dt^2) D2 F on the interior rows and A the symmetric inverse
+// of tridiag(1, 4, 1) with natural ends, the gradient of series s is
+//   G_s = Xbar_s + (6/dt^2) D2^T A mbar_s,
+// where A mbar_s is computed by the same pair of recursive filters on the
+// odd-periodic extension of mbar_s (zero at 0 and N-1).  The integrand
+// gradient is G_s (value series) or D1^T G_s (derivative series), summed per
+// integrand over the series that share it, then mapped to the five field
+// gradients.  Tile: 8 panels x 64 samples; thread (half, panel, series)
+// filters samples [32 half - 3, 32 half + 35) of the tile; the per-sample
+// integrand gradients meet in shared memory and are written per (sample,
+// panel) with coalesced stores.
+// ---------------------------------------------------------------------------
+constexpr int kAdjZ = kIirJ + 6;  // moments-adjoint values a thread keeps
+
+// G and the integrand-gradient contribution of one thread's 32 samples, from
+// its kAdjZ values z (index 0 is sample ks - 3).  EDGE: record ends inside
+// the reach (compact code, z in local memory).
+template <bool EDGE>
+__device__ __forceinline__ void adj_finish(const float (&z)[kAdjZ], const float *Xb, int s,
+                                           bool deriv, int ks, int N, float s6, float inv2h,
+                                           float *out /* stride 8 * kIirPanels */) {
+  constexpr int J = kIirJ;
+  auto zf = [&](int i) -> float {
+    return (i <= 0 || i >= N - 1) ? 0.f : z[i - (ks - 3)];
+  };
+  auto Gat = [&](int i) -> float {  // 0 <= i < N, ks - 2 <= i < ks + J + 2
+    return Xb[(size_t)i * kRec + s] + s6 * (zf(i - 1) - 2.f * zf(i) + zf(i + 1));
+  };
+  if (!EDGE) {
+    float G[J + 4];  // samples ks - 2 .. ks + J + 1
+#pragma unroll
+    for (int t = 0; t < J + 4; ++t) {
+      const int i = ks - 2 + t;
+      G[t] = Xb[(size_t)i * kRec + s] + s6 * (z[t] - 2.f * z[t + 1] + z[t + 2]);
+    }
+#pragma unroll
+    for (int t = 0; t < J; ++t)
+      out[t * 8 * kIirPanels] = deriv ? (G[t + 1] - G[t + 3]) * inv2h : G[t + 2];
+  } else {
+#pragma unroll 1
+    for (int t = 0; t < J; ++t) {
+      const int i = ks + t;
+      float c = 0.f;
+      if (i < N) {
+        if (!deriv) {
+          c = Gat(i);
+        } else {
+          if (i - 1 >= 1 && i - 1 <= N - 2) c += Gat(i - 1) * inv2h;
+          if (i + 1 >= 1 && i + 1 <= N - 2) c -= Gat(i + 1) * inv2h;
+          if (i <= 2) c += (i == 0 ? -3.f : (i == 1 ? 4.f : -1.f)) * inv2h * Gat(0);
+          if (i >= N - 3) c += (i == N - 1 ? 3.f : (i == N - 2 ? -4.f : 1.f)) * inv2h * Gat(N - 1);
+        }
+      }
+      out[t * 8 * kIirPanels] = c;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kIirThreads) k_prep_adj_iir(PrepAdjArgs<float> a) {
+  constexpr int NP = kIirPanels, H = kIirH, J = kIirJ;
+  constexpr int NR = kAdjZ + 2 * H;  // samples each thread filters
+  constexpr float rho = -0.267949192431122706f;  // sqrt(3) - 2
+  __shared__ float cs[kIirChunk * 8 * NP];  // [sample][series][panel]
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * kIirChunk;
+  const int p0 = blockIdx.y * NP;
+  const int N = a.nt;
+  if (c0 >= N) return;  // uniform across the CTA
+  {
+    const int s = tid & 7;
+    const int pl = (tid >> 3) % NP;
+    const int h = tid / (8 * NP);
+    const int ks = c0 + J * h;
+    const int p = min(p0 + pl, a.P - 1);
+    const float *Xb = a.Xbar + (size_t)p * a.ntp * kRec;
+    const bool deriv = (s == 0) || (s >= 2 && s <= 4);
+    const float inv2h = (float)(0.5 / a.dt);
+    const float s6 = (float)(6.0 / (a.dt * a.dt));
+    float *out = cs + (size_t)(ks - c0) * 8 * NP + s * NP + pl;
+    // the filters reach samples [ks - 3 - H, ks + J + 3 + H); G reads Xbar on
+    // [ks - 2, ks + J + 2)
+    const bool interior = ks - 3 - H >= 1 && ks + J + 3 + H <= N - 1;
+    if (interior) {
+      float y[kAdjZ + H];
+      float yy = 0.f;
+#pragma unroll
+      for (int t = 0; t < NR; ++t) {
+        yy = Xb[(size_t)(ks - 3 - H + t) * kRec + 8 + s] + rho * yy;
+        if (t >= H) y[t - H] = yy;
+      }
+      float xx = 0.f;
+      float z[kAdjZ];
+#pragma unroll
+      for (int t = kAdjZ + H - 1; t >= 0; --t) {
+        xx = y[t] + rho * xx;
+        if (t < kAdjZ) z[t] = -rho * xx;
+      }
+      adj_finish<false>(z, Xb, s, deriv, ks, N, s6, inv2h, out);
+    } else {
+      const int L2 = 2 * (N - 1);
+      auto mb = [&](int k) -> float {  // odd-periodic extension, zero at 0 and N - 1
+        int km = k % L2;
+        if (km < 0) km += L2;
+        float sg = 1.f;
+        if (km >= N - 1) {
+          km = L2 - km;
+          sg = -1.f;
+        }
+        if (km == 0 || km == N - 1) return 0.f;
+        return sg * Xb[(size_t)km * kRec + 8 + s];
+      };
+      float y[kAdjZ + H];
+      float yy = 0.f;
+#pragma unroll 1
+      for (int t = 0; t < NR; ++t) {
+        yy = mb(ks - 3 - H + t) + rho * yy;
+        if (t >= H) y[t - H] = yy;
+      }
+      float xx = 0.f;
+      float z[kAdjZ];
+#pragma unroll 1
+      for (int t = kAdjZ + H - 1; t >= 0; --t) {
+        xx = y[t] + rho * xx;
+        if (t < kAdjZ) z[t] = -rho * xx;
+      }
+      adj_finish<true>(z, Xb, s, deriv, ks, N, s6, inv2h, out);
+    }
+  }
+  __syncthreads();
+  // ---- integrand gradients -> field gradients, per (sample, panel) ----------
+  for (int idx = tid; idx < kIirChunk * NP; idx += kIirThreads) {
+    const int ir = idx / NP, pl = idx % NP;
+    const int i = c0 + ir, p = p0 + pl;
+    if (i >= N || p >= a.P) continue;
+    const float *c = cs + (size_t)ir * 8 * NP + pl;
+    const float qb = c[0] + c[NP];                       // Qn: series 0 and 1
+    const float lb0 = c[2 * NP] + c[5 * NP];             // L_c: series 2 + c and 5 + c
+    const float lb1 = c[3 * NP] + c[6 * NP];
+    const float lb2 = c[4 * NP] + c[7 * NP];
+    const int po = a.perm ? a.perm[p] : p;
+    const float n0 = (float)a.n[3 * p], n1 = (float)a.n[3 * p + 1], n2 = (float)a.n[3 * p + 2];
+    const float Un = (float)(a.ca * a.n[3 * p] + a.sa * a.n[3 * p + 1]);
+    const float *fb = a.fields + (size_t)i * 5 * a.P + po;
+    const float rho_ = fb[0], u0 = fb[(size_t)a.P], u1 = fb[2 * (size_t)a.P],
+                u2 = fb[3 * (size_t)a.P];
+    const float un = u0 * n0 + u1 * n1 + u2 * n2;
+    const float utn = Un + un;   // total u . n
+    const float r1 = 1.f + rho_;
+    const float lu = lb0 * u0 + lb1 * u1 + lb2 * u2;
+    float *g = a.grad_fields + (size_t)i * 5 * a.P + po;
+    g[0] = qb * utn + lu * utn;                               // d/drho'
+    g[(size_t)a.P] = r1 * (qb * n0 + lb0 * utn + lu * n0);   // d/du'_1
+    g[2 * (size_t)a.P] = r1 * (qb * n1 + lb1 * utn + lu * n1);
+    g[3 * (size_t)a.P] = r1 * (qb * n2 + lb2 * utn + lu * n2);
+    g[4 * (size_t)a.P] = lb0 * n0 + lb1 * n1 + lb2 * n2;     // d/dp' (dL_c/dp' = n_c)
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -589,6 +749,11 @@ cudaError_t launch_prep(const PrepArgs<T> &a0, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_prep_adjoint(const PrepAdjArgs<T> &a0, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    dim3 grid((a0.nt + kIirChunk - 1) / kIirChunk, (a0.P + kIirPanels - 1) / kIirPanels);
+    k_prep_adj_iir<<<grid, kIirThreads, 0, s>>>(a0);
+    return cudaGetLastError();
+  }
   PrepAdjArgs<T> a = a0;
   a.chunk = PrepChunk<T>::v;
   const size_t smem = (size_t)(a.chunk + 6 + Prec<T>::halo) * kThreads * sizeof(T);
