@@ -61,7 +61,7 @@ struct fwh_ctx {
   double *d_y = nullptr, *d_n = nullptr, *d_dS = nullptr, *d_x = nullptr;
   double *d_Rmax = nullptr, *d_Rmin = nullptr;
   int *d_perm = nullptr, *d_err = nullptr;
-  Buf coef, X, G, nvalid, sets, stage_in, stage_out, stage_grad, tmap, imax;
+  Buf coef, X, G, nvalid, sets, sord, stage_in, stage_out, stage_grad, tmap, imax;
   const void *tmap_X = nullptr;  // X buffer / rows / box the device descriptor describes
   int tmap_box = 0;
   long long tmap_rows = 0;
@@ -215,6 +215,15 @@ fwh_status plan(fwh_handle h, const FwdConfig &c, cudaStream_t s) {
   const int nsets = (int)h->set_begin.size() - 1;
   CK(h, ensure(h->sets, bytes));
   CK(h, cudaMemcpy(h->sets.p, h->set_begin.data(), bytes, cudaMemcpyHostToDevice));
+  {  // work order: sets by descending panel count
+    std::vector<int> ord(nsets);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+      return h->set_begin[x + 1] - h->set_begin[x] > h->set_begin[y + 1] - h->set_begin[y];
+    });
+    CK(h, ensure(h->sord, ord.size() * sizeof(int)));
+    CK(h, cudaMemcpy(h->sord.p, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   CK(h, ensure(h->imax, (size_t)nsets * h->O * sizeof(int)));
   if (h->precision == FWH_FP64)
     CK(h, launch_plan<double>(reinterpret_cast<double *>(h->coef.p),
@@ -334,6 +343,7 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
   fa.p_out = d_pout;
   fa.n_valid = reinterpret_cast<const int *>(h->nvalid.p);
   fa.set_begin = reinterpret_cast<const int *>(h->sets.p);
+  fa.set_order = reinterpret_cast<const int *>(h->sord.p);
   fa.i0max_tab = reinterpret_cast<const int *>(h->imax.p);
   fa.err = h->d_err;
   fa.nsets = (int)h->set_begin.size() - 1;
@@ -798,7 +808,8 @@ void fwh_destroy(fwh_handle h) {
     if (p) cudaFree(p);
   if (h->d_perm) cudaFree(h->d_perm);
   if (h->d_err) cudaFree(h->d_err);
-  for (Buf *b : {&h->coef, &h->X, &h->G, &h->nvalid, &h->sets, &h->stage_in, &h->stage_out,
+  for (Buf *b : {&h->coef, &h->X, &h->G, &h->nvalid, &h->sets, &h->sord, &h->stage_in,
+                 &h->stage_out,
                  &h->stage_grad, &h->tmap, &h->imax})
     release(*b);
   for (int i = 0; i < 4; ++i)
@@ -849,6 +860,7 @@ fwh_status batch_build(int n, const fwh_handle *hs, const void *const *fields,
     fa.p_out = p_out[i];
     fa.n_valid = reinterpret_cast<const int *>(h->nvalid.p);
     fa.set_begin = reinterpret_cast<const int *>(h->sets.p);
+    fa.set_order = reinterpret_cast<const int *>(h->sord.p);
     fa.i0max_tab = reinterpret_cast<const int *>(h->imax.p);
     fa.err = h0->d_err;
     fa.nsets = (int)h->set_begin.size() - 1;

@@ -250,10 +250,14 @@ struct Item {
   int sidx, p_begin, p_end, o_begin, o_end, opw, nobs, k_begin, k_end;
   __device__ __forceinline__ Item(const FwdArgs<T> &a, int item, int w) {
     const int ng = a.n_obs_groups;
+    // observer group fastest (groups share the set's X rows in L2), then the
+    // time segments of one set, then the sets, largest first so that the
+    // last CTAs to start are the shortest
     const int g = item % ng;
     const int rest = item / ng;
-    sidx = rest % a.nsets;
-    const int q = rest / a.nsets;
+    const int q = rest % a.n_segs;
+    const int r2 = rest / a.n_segs;
+    sidx = a.set_order ? a.set_order[r2] : r2;
     p_begin = a.set_begin[sidx];
     p_end = a.set_begin[sidx + 1];
     opw = a.obs_per_cta / NW;

@@ -80,6 +80,7 @@ struct FwdArgs {
   double *p_out;        // [O][nt]
   const int *n_valid;   // [O]
   const int *set_begin; // [nsets + 1] panel-set boundaries (sorted order)
+  const int *set_order; // [nsets] sets by descending panel count (null: index order)
   const int *i0max_tab; // [nsets][O] largest shift of each (panel set, observer)
   int *err;
   int nsets, O, ntp, nt;
