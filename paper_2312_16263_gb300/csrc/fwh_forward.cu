@@ -942,6 +942,7 @@ __global__ void __maxnreg__(200)
 // to 128 (three CTAs of five warps per SM), tk 8 168 (two).
 constexpr FwdConfig kCfgF32[] = {
     {1, 4, 4, 9, 224, 4, 3, 3, 0},
+    {1, 4, 4, 9, 224, 2, 3, 3, 0},
     {1, 4, 4, 9, 224, 4, 3, 4, 0},
     {2, 4, 4, 9, 224, 4, 2, 3, 0},
     {2, 4, 8, 9, 224, 4, 3, 3, 0},
