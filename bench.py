@@ -375,7 +375,8 @@ def main():
         "fp64": {"value": evals * ws / (max_over_ranks(ms64, ws) / 1e3), "unit": UNIT,
                  "ms_per_step": ms64, "kernel_ms": fwd64,
                  "achieved_tflops": evals * FLOP_PER_EVAL / (fwd64 / 1e3) / 1e12,
-                 "peak_tflops": FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64"},
+                 "peak_tflops": FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64",
+                 "frac": evals * FLOP_PER_EVAL / (fwd64 / 1e3) / 1e12 / FP64_PEAK_TFLOPS},
         "accuracy": {"mixed_vs_fp64_rel_l2_max": float(rel_mixed_fp64.max()),
                      "mixed_vs_fp64_rel_l2_median": float(np.median(rel_mixed_fp64))},
         "e2e": {"value": evals * ws / (e2e_ms_max / 1e3), "unit": UNIT,
