@@ -24,10 +24,11 @@ template <> __device__ __forceinline__ int i0_of<double>(double v) { return (int
 template <typename T>
 __global__ void k_grad_pad(const double *grad_p, const int *n_valid, T *Gt, int O, int nt,
                            int ntp) {
-  const int o = blockIdx.y;
-  const int nv = n_valid[o];
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ntp; j += gridDim.x * blockDim.x)
-    Gt[(size_t)o * ntp + j] = (j < nv && j < nt) ? (T)grad_p[(size_t)o * nt + j] : T(0);
+  for (int o = blockIdx.y; o < O; o += gridDim.y) {  // grid y is capped at 65535
+    const int nv = n_valid[o];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ntp; j += gridDim.x * blockDim.x)
+      Gt[(size_t)o * ntp + j] = (j < nv && j < nt) ? (T)grad_p[(size_t)o * nt + j] : T(0);
+  }
 }
 
 // One CTA per (panel, group of 8 chunks), one warp per chunk.  The panel's
@@ -115,7 +116,7 @@ cudaError_t launch_adjoint(const AdjArgs<T> &a, cudaStream_t s) {
   constexpr int TK = sizeof(T) == 4 ? 4 : 2;
   constexpr int CH = 32 * TK;
   T *Gt = a.Gt;
-  dim3 gg((a.ntp + 255) / 256, a.O);
+  dim3 gg((a.ntp + 255) / 256, a.O < 65535 ? a.O : 65535);
   k_grad_pad<T><<<gg, 256, 0, s>>>(a.grad_p, a.n_valid, Gt, a.O, a.nt, a.ntp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -241,6 +241,8 @@ fwh_status plan(fwh_handle h, const FwdConfig &c, cudaStream_t s) {
 // Per-nt window and workspace.  ntp is a multiple of 256, hence of every
 // forward chunk (32 x TK samples) and prep chunk.
 fwh_status prepare_nt(fwh_handle h, int64_t nt) {
+  if (h->precision == FWH_MIXED && h->P * ((nt + 255) / 256 * 256) >= ((int64_t)1 << 32))
+    return fail(h, FWH_ERR_ARG, "panels x padded steps must stay below 2^32 per handle");
   if (h->nt != nt) {
     h->h_nvalid.assign(h->O, 0);
     h->h_tstart.assign(h->O, 0.0);
@@ -257,8 +259,6 @@ fwh_status prepare_nt(fwh_handle h, int64_t nt) {
     CK(h, cudaMemcpy(h->nvalid.p, h->h_nvalid.data(), h->O * sizeof(int),
                      cudaMemcpyHostToDevice));
     const int64_t ntp = (nt + 255) / 256 * 256;  // a multiple of every chunk length
-    if (h->precision == FWH_MIXED && h->P * ntp >= ((int64_t)1 << 32))
-      return fail(h, FWH_ERR_ARG, "panels x padded steps must stay below 2^32 per handle");
     h->nt = nt;
     h->ntp = (int)ntp;
   }

@@ -83,44 +83,45 @@ __device__ __forceinline__ void store_i0<double>(double *slot, int i0) {
 template <typename T>
 __global__ void __launch_bounds__(128) k_coef(GeomArgs a, T *coef) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int o = blockIdx.y;
   if (p >= a.P) return;
-  const double d[3] = {a.x[3 * o] - a.y[3 * p], a.x[3 * o + 1] - a.y[3 * p + 1],
-                       a.x[3 * o + 2] - a.y[3 * p + 2]};
-  double R, Rh[3];
-  convected(d, a.mach, a.ca, a.sa, R, Rh);
-  const double M0 = a.mach;
-  const double U[3] = {a.ca, a.sa, 0.0};
-  const double URh = U[0] * Rh[0] + U[1] * Rh[1];
-  const double MR = -M0 * URh;               // M = -M0 U (surface moves at -U0)
-  const double D = 1.0 - MR;
-  const double S = a.dS[p] * 0.079577471545947667884441881686257181;  // 1/(4 pi)
-  const double iR = 1.0 / R, iD = 1.0 / D;
-  const double k1 = S * iR * iD * iD;        // S / (R D^2)
-  const double k2 = k1 * iR;                 // S / (R^2 D^2)
-  const double mrm = MR - M0 * M0;           // M_R - M^2
-  double c[8];
-  c[0] = k1;
-  c[1] = k2 * mrm * iD / M0;
-  for (int i = 0; i < 3; ++i) {
-    c[2 + i] = k1 * M0 * Rh[i];
-    c[5 + i] = k2 * (Rh[i] + M0 * U[i] + Rh[i] * mrm * iD);
+  for (int o = blockIdx.y; o < a.O; o += gridDim.y) {  // grid y is capped at 65535
+    const double d[3] = {a.x[3 * o] - a.y[3 * p], a.x[3 * o + 1] - a.y[3 * p + 1],
+                         a.x[3 * o + 2] - a.y[3 * p + 2]};
+    double R, Rh[3];
+    convected(d, a.mach, a.ca, a.sa, R, Rh);
+    const double M0 = a.mach;
+    const double U[3] = {a.ca, a.sa, 0.0};
+    const double URh = U[0] * Rh[0] + U[1] * Rh[1];
+    const double MR = -M0 * URh;               // M = -M0 U (surface moves at -U0)
+    const double D = 1.0 - MR;
+    const double S = a.dS[p] * 0.079577471545947667884441881686257181;  // 1/(4 pi)
+    const double iR = 1.0 / R, iD = 1.0 / D;
+    const double k1 = S * iR * iD * iD;        // S / (R D^2)
+    const double k2 = k1 * iR;                 // S / (R^2 D^2)
+    const double mrm = MR - M0 * M0;           // M_R - M^2
+    double c[8];
+    c[0] = k1;
+    c[1] = k2 * mrm * iD / M0;
+    for (int i = 0; i < 3; ++i) {
+      c[2 + i] = k1 * M0 * Rh[i];
+      c[5 + i] = k2 * (Rh[i] + M0 * U[i] + Rh[i] * mrm * iD);
+    }
+    const double q = M0 * (a.Rmax[o] - R) / a.dt;
+    double fl = floor(q);
+    double f = q - fl;
+    const double aw = 1.0 - f, bw = f;
+    const double h26 = a.dt * a.dt / 6.0;
+    T *rec = coef + ((size_t)p * a.O + o) * kRec;
+    for (int i = 0; i < 8; ++i) rec[slot::c + i] = (T)c[i];
+    rec[slot::a] = (T)aw;
+    rec[slot::b] = (T)bw;
+    rec[slot::cc] = (T)((aw * aw * aw - aw) * h26);
+    rec[slot::dd] = (T)((bw * bw * bw - bw) * h26);
+    rec[slot::off] = (T)0;
+    rec[14] = (T)0;
+    rec[15] = (T)0;
+    store_i0<T>(rec + slot::i0, (int)fl);
   }
-  const double q = M0 * (a.Rmax[o] - R) / a.dt;
-  double fl = floor(q);
-  double f = q - fl;
-  const double aw = 1.0 - f, bw = f;
-  const double h26 = a.dt * a.dt / 6.0;
-  T *rec = coef + ((size_t)p * a.O + o) * kRec;
-  for (int i = 0; i < 8; ++i) rec[slot::c + i] = (T)c[i];
-  rec[slot::a] = (T)aw;
-  rec[slot::b] = (T)bw;
-  rec[slot::cc] = (T)((aw * aw * aw - aw) * h26);
-  rec[slot::dd] = (T)((bw * bw * bw - bw) * h26);
-  rec[slot::off] = (T)0;
-  rec[14] = (T)0;
-  rec[15] = (T)0;
-  store_i0<T>(rec + slot::i0, (int)fl);
 }
 
 }  // namespace
@@ -134,7 +135,7 @@ cudaError_t launch_window(const GeomArgs &a, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_coef(const GeomArgs &a, T *coef, cudaStream_t s) {
   if (a.O <= 0 || a.P <= 0) return cudaSuccess;
-  dim3 grid((a.P + 127) / 128, a.O);
+  dim3 grid((a.P + 127) / 128, a.O < 65535 ? a.O : 65535);
   k_coef<T><<<grid, 128, 0, s>>>(a, coef);
   return cudaGetLastError();
 }

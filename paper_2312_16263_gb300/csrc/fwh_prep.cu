@@ -24,6 +24,8 @@
 // per 32-sample block (see the kernel), written as whole X tiles.
 #include "fwh_internal.cuh"
 
+#include <cstdint>
+
 namespace fwh {
 
 __constant__ float c_inv_piv_f[kPivTab];
@@ -112,8 +114,9 @@ __global__ void __launch_bounds__(PrepTile<T>::panels * 8) k_prep(PrepArgs<T> a)
   constexpr int H = Prec<T>::halo;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x;
-  const int p0 = blockIdx.x * NP;
-  const int c0 = blockIdx.y * a.chunk;
+  const int n_pt = (a.P + NP - 1) / NP;  // 1D grid: panel tile fastest, then chunk
+  const int p0 = (int)(blockIdx.x % n_pt) * NP;
+  const int c0 = (int)(blockIdx.x / n_pt) * a.chunk;
   const int c1 = min(c0 + a.chunk, a.ntp);
   const int nt = a.nt;
 
@@ -295,8 +298,9 @@ __global__ void __launch_bounds__(kIirThreads, 4) k_prep_iir(PrepArgs<float> a) 
   float *tile = reinterpret_cast<float *>(smem_raw);
   float *sb = tile + NP * kIirChunk * kRec;
   const int tid = threadIdx.x;
-  const int c0 = blockIdx.x * kIirChunk;
-  const int p0 = blockIdx.y * NP;
+  const int n_ct = a.ntp / kIirChunk;  // 1D grid: chunk fastest, then panel tile
+  const int c0 = (int)(blockIdx.x % n_ct) * kIirChunk;
+  const int p0 = (int)(blockIdx.x / n_ct) * NP;
   const int N = a.nt;
   if (c0 < N) {
     // staged integrand rows: the tile's filter reach plus FD neighbours, and
@@ -454,9 +458,10 @@ __global__ void __launch_bounds__(kThreads) k_prep_adj(PrepAdjArgs<T> a) {
   T *zb = reinterpret_cast<T *>(smem_raw);
   const int tid = threadIdx.x;
   const int s = tid & 7;
-  const int p = blockIdx.x * kPanelsPerCta + (tid >> 3);
+  const int n_pt = (a.P + kPanelsPerCta - 1) / kPanelsPerCta;  // 1D grid, panel tile fastest
+  const int p = (int)(blockIdx.x % n_pt) * kPanelsPerCta + (tid >> 3);
   const bool live = p < a.P;
-  const int c0 = blockIdx.y * a.chunk;
+  const int c0 = (int)(blockIdx.x / n_pt) * a.chunk;
   const int nt = a.nt;
   const int ce = min(c0 + a.chunk, nt);
   if (c0 >= nt) return;  // uniform across the CTA
@@ -620,8 +625,9 @@ __global__ void __launch_bounds__(kIirThreads) k_prep_adj_iir(PrepAdjArgs<float>
   constexpr float rho = -0.267949192431122706f;  // sqrt(3) - 2
   __shared__ float cs[kIirChunk * 8 * NP];  // [sample][series][panel]
   const int tid = threadIdx.x;
-  const int c0 = blockIdx.x * kIirChunk;
-  const int p0 = blockIdx.y * NP;
+  const int n_ct = (a.nt + kIirChunk - 1) / kIirChunk;  // 1D grid: chunk fastest
+  const int c0 = (int)(blockIdx.x % n_ct) * kIirChunk;
+  const int p0 = (int)(blockIdx.x / n_ct) * NP;
   const int N = a.nt;
   if (c0 >= N) return;  // uniform across the CTA
   {
@@ -726,8 +732,10 @@ cudaError_t launch_prep(const PrepArgs<T> &a0, cudaStream_t s) {
                                          (int)smem);
     if (e != cudaSuccess) return e;
     if (a0.ntp % kIirChunk != 0) return cudaErrorInvalidValue;
-    dim3 grid(a0.ntp / kIirChunk, (a0.P + kIirPanels - 1) / kIirPanels);
-    k_prep_iir<<<grid, kIirThreads, smem, s>>>(a0);
+    const long blocks = (long)(a0.ntp / kIirChunk) * ((a0.P + kIirPanels - 1) / kIirPanels);
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > INT32_MAX) return cudaErrorInvalidValue;
+    k_prep_iir<<<(unsigned)blocks, kIirThreads, smem, s>>>(a0);
     return cudaGetLastError();
   } else {
     constexpr int NP = PrepTile<T>::panels;
@@ -741,8 +749,10 @@ cudaError_t launch_prep(const PrepArgs<T> &a0, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_prep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((a.P + NP - 1) / NP, (a.ntp + a.chunk - 1) / a.chunk);
-    k_prep<T><<<grid, NP * 8, smem, s>>>(a);
+    const long blocks = (long)((a.P + NP - 1) / NP) * ((a.ntp + a.chunk - 1) / a.chunk);
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > INT32_MAX) return cudaErrorInvalidValue;
+    k_prep<T><<<(unsigned)blocks, NP * 8, smem, s>>>(a);
     return cudaGetLastError();
   }
 }
@@ -750,8 +760,11 @@ cudaError_t launch_prep(const PrepArgs<T> &a0, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_prep_adjoint(const PrepAdjArgs<T> &a0, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    dim3 grid((a0.nt + kIirChunk - 1) / kIirChunk, (a0.P + kIirPanels - 1) / kIirPanels);
-    k_prep_adj_iir<<<grid, kIirThreads, 0, s>>>(a0);
+    const long blocks =
+        (long)((a0.nt + kIirChunk - 1) / kIirChunk) * ((a0.P + kIirPanels - 1) / kIirPanels);
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > INT32_MAX) return cudaErrorInvalidValue;
+    k_prep_adj_iir<<<(unsigned)blocks, kIirThreads, 0, s>>>(a0);
     return cudaGetLastError();
   }
   PrepAdjArgs<T> a = a0;
@@ -760,8 +773,11 @@ cudaError_t launch_prep_adjoint(const PrepAdjArgs<T> &a0, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_prep_adj<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((a.P + kPanelsPerCta - 1) / kPanelsPerCta, (a.nt + a.chunk - 1) / a.chunk);
-  k_prep_adj<T><<<grid, kThreads, smem, s>>>(a);
+  const long blocks =
+      (long)((a.P + kPanelsPerCta - 1) / kPanelsPerCta) * ((a.nt + a.chunk - 1) / a.chunk);
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks > INT32_MAX) return cudaErrorInvalidValue;
+  k_prep_adj<T><<<(unsigned)blocks, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -77,7 +77,7 @@ def test_workload1_parity(dev, prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", ["ragged", "min_nt", "one_obs", "unstructured", "high_mach",
-                                  "many_obs"])
+                                  "many_obs", "one_panel"])
 def test_edge_cases(dev, prec, case):
     rng = np.random.default_rng(zlib.crc32(case.encode()))
     mach, aoa, dt = 0.35, -12 * DEG, 0.03
@@ -101,6 +101,9 @@ def test_edge_cases(dev, prec, case):
     elif case == "many_obs":
         obs = observers_circle(40.0, 150)
         nt = 260
+    elif case == "one_panel":
+        from fwh_inputs.geometry import Surface
+        surf = Surface(np.array([[0.2, -0.1, 0.3]]), np.array([[0.0, 0.6, 0.8]]), np.array([0.05]))
     flow = FlowCase(mach, aoa)
     f = surface_fields("monopole", surf.centroids, flow, 0.01, 2 * np.pi, dt, nt)
     f += rng.normal(size=f.shape) * 1e-4      # break symmetry, exercise all terms
@@ -202,3 +205,42 @@ def test_every_tile_config_agrees(dev, prec):
     chosen = s.autotune(w.nt)
     assert 0 <= chosen < n
     s.check()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_empty_observer_window_gives_zeros(dev, prec):
+    """A record shorter than the arrival-time spread over the surface leaves no
+    valid observer bin (N_o = 0): the output is all zeros, like the oracle's."""
+    surf = uv_sphere(1.0, 6, 10)
+    mach, aoa, dt, nt = 0.5, 0.0, 1e-3, 40          # spread ~ 1000 samples >> nt
+    obs = observers_circle(30.0, 4)
+    f = np.random.default_rng(3).normal(size=(nt, 5, surf.n_panels)) * 1e-3
+    p, nv, p_ref, nv_ref, _ = _run_case(dev, surf, mach, aoa, dt, f, obs, prec)
+    assert np.all(nv == 0) and np.all(nv_ref == 0)
+    assert np.all(p == 0.0)
+
+
+def test_oversized_mixed_problem_is_refused_and_the_handle_survives(dev):
+    """Mixed handles address series rows with 32-bit indices: panels x steps
+    (rounded up to 256) at or above 2^32 is refused before any kernel runs, and
+    the handle keeps working for a valid length afterwards."""
+    import ctypes
+    from paper_2312_16263_gb300 import FWH, _abi
+    n = 1 << 21                                      # 2M panels on a sphere
+    th = np.arccos(1 - 2 * (np.arange(n) + 0.5) / n)
+    ph = np.pi * (1 + 5 ** 0.5) * np.arange(n)
+    nrm = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
+    s = FWH(nrm * 1.0, nrm.copy(), np.full(n, 4 * np.pi / n), 0.3, 0.1, 0.02, "mixed",
+            observers=np.array([[0.0, -20.0, 0.0]]))
+    dummy = torch.zeros(16, device=dev)
+    out = torch.zeros(2, device=dev, dtype=torch.float64)
+    st = s.lib.fwh_forward(s.h, ctypes.c_void_p(dummy.data_ptr()), 2049,
+                           ctypes.c_void_p(out.data_ptr()), None)
+    assert st == _abi.FWH_ERR_ARG and b"2^32" in s.lib.fwh_last_error(s.h)
+    nt = 8
+    f = torch.zeros((nt, 5, n), dtype=torch.float32, device=dev)
+    f[:, 4] = 1e-3
+    p = s.forward(f)
+    s.check()
+    assert torch.isfinite(p).all()
+    s.close()
