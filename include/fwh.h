@@ -68,7 +68,8 @@ enum { FWH_FP64 = 0, FWH_MIXED = 1 };
  * which must equal 1/M0 within 1e-12 relative (Sec. II D), dt > 0 the
  * nondimensional sampling interval, precision FWH_FP64 or FWH_MIXED
  * (mixed: FP32 fields and integrand arithmetic, FP64 arrival times and
- * interpolation weights, compensated per-bin accumulation, FP64 output).
+ * interpolation weights, per-bin FP32 sums over one panel set at a time added
+ * into FP64 output bins).
  * Errors: FWH_ERR_ARG on any invalid value (no handle is created),
  * FWH_ERR_OOM / FWH_ERR_CUDA on allocation or device failure.
  */
@@ -93,8 +94,10 @@ fwh_status fwh_set_observers(fwh_handle h, int64_t n_obs, const double *xyz);
  * [nt][5][P] (double for FWH_FP64, float for FWH_MIXED), nt >= 3.
  * Covers the "compute Noise", "compute t", "interp pressure signal" and
  * surface-integration stages (Sec. III B, III C).
- * Errors: FWH_ERR_STATE before fwh_set_observers, FWH_ERR_ARG for nt < 3 or
- * null pointers, FWH_ERR_CUDA / FWH_ERR_OOM on device failure.
+ * Errors: FWH_ERR_STATE before fwh_set_observers, FWH_ERR_ARG for nt < 3,
+ * null pointers, or (FWH_MIXED) n_panels x round_up(nt, 256) >= 2^32 (series
+ * rows are addressed with 32-bit indices; checked before any work, the handle
+ * stays usable), FWH_ERR_CUDA / FWH_ERR_OOM on device failure.
  */
 fwh_status fwh_forward(fwh_handle h, const void *fields, int64_t nt, double *p_out,
                        void *stream);
