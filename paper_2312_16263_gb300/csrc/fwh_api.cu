@@ -87,6 +87,8 @@ struct fwh_ctx {
   std::map<std::vector<uintptr_t>, Graph> graphs;
   std::map<std::vector<uintptr_t>, BatchPlan> bplans;
   cudaStream_t side = nullptr;
+  cudaStream_t copy = nullptr;              // host-field slabs (fwh_forward)
+  std::vector<cudaEvent_t> slab_ev;         // one per slab, plus the start
   cudaEvent_t bev[2] = {nullptr, nullptr};
 };
 
@@ -298,8 +300,15 @@ fwh_status ensure_tmap(fwh_handle h, int box_rows) {
   return FWH_OK;
 }
 
+// Host fields of a mixed handle are copied in slabs of kSlab source frames on
+// a copy stream; the series of slab q are prepared as soon as slab q + 1 (which
+// holds the filters' reach beyond it) has landed, so the prep runs under the
+// copy of the later slabs and only the forward scatter waits for the last one.
+constexpr int kSlab = 256;
+
 template <typename T>
-fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStream_t s) {
+fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStream_t s,
+                       const T *host_fields = nullptr) {
   const bool fp64 = sizeof(T) == 8;
   const int cfg = effective_cfg(h, h->ntp);
   const FwdConfig c = fwd_config(fp64, cfg);
@@ -334,7 +343,41 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
   pa.ca = h->ca;
   pa.sa = h->sa;
   pa.dt = h->dt;
-  CK(h, launch_prep<T>(pa, s));
+  if (host_fields == nullptr) {
+    CK(h, launch_prep<T>(pa, s));
+  } else {
+    const int nslab = (int)((h->nt + kSlab - 1) / kSlab);
+    const size_t row = (size_t)5 * h->P * sizeof(T);
+    if (!h->copy) CK(h, cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking));
+    while ((int)h->slab_ev.size() < nslab + 1) {
+      cudaEvent_t e;
+      CK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      h->slab_ev.push_back(e);
+    }
+    // the staging buffer is free once the work already on `s` is done
+    CK(h, cudaEventRecord(h->slab_ev[nslab], s));
+    CK(h, cudaStreamWaitEvent(h->copy, h->slab_ev[nslab], 0));
+    // copy slab q, then prepare slab q - 1, whose filter reach (83 frames)
+    // ends inside slab q; the last slab after the last copy.  Issuing them
+    // interleaved keeps the overlap when a pageable source makes each copy
+    // call return only after staging it.
+    constexpr int cps = kSlab / 64;  // 64-sample prep chunks per slab
+    for (int q = 0; q < nslab; ++q) {
+      const int64_t r0 = (int64_t)q * kSlab, r1 = std::min<int64_t>(h->nt, r0 + kSlab);
+      CK(h, cudaMemcpyAsync(const_cast<T *>(d_fields) + r0 * 5 * h->P,
+                            host_fields + r0 * 5 * h->P, (size_t)(r1 - r0) * row,
+                            cudaMemcpyHostToDevice, h->copy));
+      CK(h, cudaEventRecord(h->slab_ev[q], h->copy));
+      if (q == 0) continue;
+      CK(h, cudaStreamWaitEvent(s, h->slab_ev[q], 0));
+      pa.c_lo = (q - 1) * cps;
+      pa.c_hi = q * cps;
+      CK(h, launch_prep<T>(pa, s));
+    }
+    pa.c_lo = (nslab - 1) * cps;
+    pa.c_hi = h->ntp / 64;
+    CK(h, launch_prep<T>(pa, s));
+  }
   if (tev) CK(h, cudaEventRecord(tev[1], s));
   FwdArgs<T> fa{};
   fa.tmX = h->tmap.p;
@@ -616,9 +659,12 @@ fwh_status fwh_forward(fwh_handle h, const void *fields, int64_t nt, double *p_o
   const bool din = is_device_ptr(fields), dout = is_device_ptr(p_out);
   const void *df = fields;
   double *dp = p_out;
+  // mixed handles overlap the copy of host fields with the series prep
+  const bool slabs = !din && h->precision == FWH_MIXED && nt >= 2 * kSlab;
   if (!din) {
     CK(h, ensure(h->stage_in, fbytes));
-    CK(h, cudaMemcpyAsync(h->stage_in.p, fields, fbytes, cudaMemcpyHostToDevice, s));
+    if (!slabs)
+      CK(h, cudaMemcpyAsync(h->stage_in.p, fields, fbytes, cudaMemcpyHostToDevice, s));
     df = h->stage_in.p;
   }
   if (!dout) {
@@ -627,7 +673,8 @@ fwh_status fwh_forward(fwh_handle h, const void *fields, int64_t nt, double *p_o
   }
   st = h->precision == FWH_FP64
            ? run_forward<double>(h, reinterpret_cast<const double *>(df), dp, s)
-           : run_forward<float>(h, reinterpret_cast<const float *>(df), dp, s);
+           : run_forward<float>(h, reinterpret_cast<const float *>(df), dp, s,
+                                slabs ? reinterpret_cast<const float *>(fields) : nullptr);
   if (st != FWH_OK) return st;
   if (!dout) {
     CK(h, cudaMemcpyAsync(p_out, dp, obytes, cudaMemcpyDeviceToHost, s));
@@ -818,6 +865,8 @@ void fwh_destroy(fwh_handle h) {
   for (int i = 0; i < 2; ++i)
     if (h->bev[i]) cudaEventDestroy(h->bev[i]);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->copy) cudaStreamDestroy(h->copy);
+  for (cudaEvent_t e : h->slab_ev) cudaEventDestroy(e);
   delete h;
 }
 

@@ -70,6 +70,7 @@ struct PrepArgs {
   T *X;                 // [P][ntp][16]
   int P, nt, ntp, chunk;
   double ca, sa, dt;
+  int c_lo, c_hi;       // FP32: 64-sample chunks [c_lo, c_hi) to prepare (0, 0: all)
 };
 
 template <typename T>

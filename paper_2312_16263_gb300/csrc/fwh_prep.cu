@@ -298,8 +298,8 @@ __global__ void __launch_bounds__(kIirThreads, 4) k_prep_iir(PrepArgs<float> a) 
   float *tile = reinterpret_cast<float *>(smem_raw);
   float *sb = tile + NP * kIirChunk * kRec;
   const int tid = threadIdx.x;
-  const int n_ct = a.ntp / kIirChunk;  // 1D grid: chunk fastest, then panel tile
-  const int c0 = (int)(blockIdx.x % n_ct) * kIirChunk;
+  const int n_ct = a.c_hi - a.c_lo;  // 1D grid: chunk fastest, then panel tile
+  const int c0 = (a.c_lo + (int)(blockIdx.x % n_ct)) * kIirChunk;
   const int p0 = (int)(blockIdx.x / n_ct) * NP;
   const int N = a.nt;
   if (c0 < N) {
@@ -732,10 +732,15 @@ cudaError_t launch_prep(const PrepArgs<T> &a0, cudaStream_t s) {
                                          (int)smem);
     if (e != cudaSuccess) return e;
     if (a0.ntp % kIirChunk != 0) return cudaErrorInvalidValue;
-    const long blocks = (long)(a0.ntp / kIirChunk) * ((a0.P + kIirPanels - 1) / kIirPanels);
-    if (blocks <= 0) return cudaSuccess;
+    PrepArgs<float> a = a0;
+    if (a.c_hi == 0) {
+      a.c_lo = 0;
+      a.c_hi = a.ntp / kIirChunk;
+    }
+    if (a.c_lo < 0 || a.c_hi > a.ntp / kIirChunk || a.c_lo >= a.c_hi) return cudaErrorInvalidValue;
+    const long blocks = (long)(a.c_hi - a.c_lo) * ((a.P + kIirPanels - 1) / kIirPanels);
     if (blocks > INT32_MAX) return cudaErrorInvalidValue;
-    k_prep_iir<<<(unsigned)blocks, kIirThreads, smem, s>>>(a0);
+    k_prep_iir<<<(unsigned)blocks, kIirThreads, smem, s>>>(a);
     return cudaGetLastError();
   } else {
     constexpr int NP = PrepTile<T>::panels;

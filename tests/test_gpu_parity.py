@@ -140,6 +140,27 @@ def test_host_pointer_path_matches_device(dev, prec):
     assert torch.allclose(p_host, p_dev, rtol=0, atol=1e-14 * p_dev.abs().max().item())
 
 
+def test_host_slab_pipeline_matches_device(dev):
+    """Host FP32 fields of 512 frames or more are copied in 256-frame slabs
+    whose series prep overlaps the later copies; the series must come out as
+    from one copy: exact-slab, ragged-last-slab (one frame and 188 frames)
+    and below-threshold record lengths, from pinned and pageable memory."""
+    w = workload(4)
+    from paper_2312_16263_gb300 import FWH
+    s = FWH.from_workload(w, "mixed")
+    f_all = w.fields(dtype="float32")
+    for nt in (511, 512, 513, 700, 1024):
+        f = f_all[:nt].contiguous()
+        p_dev = s.forward(f.to(dev)).cpu()
+        scale = p_dev.abs().max().item()
+        assert scale > 0, nt
+        for src in (f, f.pin_memory()):
+            p_host = s.forward(src)
+            assert p_host.device.type == "cpu"
+            # equal up to the order of the FP64 output atomics
+            assert torch.allclose(p_host, p_dev, rtol=0, atol=1e-13 * scale), nt
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_backward_matches_oracle_adjoint(dev, prec):
     rng = np.random.default_rng(5)
