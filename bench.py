@@ -38,6 +38,16 @@ FLOP_PER_EVAL = 40          # 20 FMA: 8 + 8 (signal, spline moment) + 4 (interpo
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # FP64 FMA roof: nominal GB300 FP64 rate
 FP64_PEAK_TFLOPS = 1.25
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this GPU pool (GB/s), else the earlier
+    GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
 PROFILE = os.path.join(ROOT, "profiles", "forward_kernel_workload2.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_2312_16263_gb300", "csrc", "fwh_forward.cu")
 
@@ -314,6 +324,11 @@ def main():
     fwd_ms = tt["forward_ms"] / max(1, tt["calls"])
     prep_ms = tt["prep_ms"] / max(1, tt["calls"])
     achieved = evals * FLOP_PER_EVAL / (fwd_ms / 1e3) / 1e12
+    # series prep: FP32 fields read once, FP32 series rows (16 values per panel
+    # and padded step) written once
+    ntp = (w.nt + 255) // 256 * 256
+    prep_bytes = w.nt * 5 * w.surface.n_panels * 4 + w.surface.n_panels * ntp * 16 * 4
+    hbm_gbs, hbm_src = hbm_peak_gbs()
     traffic = profile_traffic()
     p_mixed = out.cpu().numpy()
     _, nv = s.window(w.nt)
@@ -351,8 +366,11 @@ def main():
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     e2e_ms_max = max_over_ranks(e2e_s * 1e3, ws)
-    assert torch.equal(oh, out.cpu()) or np.allclose(oh.numpy(), p_mixed, rtol=0,
-                                                     atol=1e-12 * np.abs(p_mixed).max())
+    # the host path scatters shorter time segments (overlapped with the copy),
+    # which splits FP32 per-bin partial sums differently: equal to FP32 rounding
+    e2e_den = np.linalg.norm(p_mixed, axis=1)
+    e2e_rel = np.linalg.norm(oh.numpy() - p_mixed, axis=1) / np.where(e2e_den > 0, e2e_den, 1)
+    assert e2e_rel.max() <= 1e-5, e2e_rel.max()
     clocks = clk.summary()
 
     line = {
@@ -383,7 +401,13 @@ def main():
                 "h2d_bytes_per_step": int(fh.numel() * fh.element_size()),
                 "d2h_bytes_per_step": int(oh.numel() * oh.element_size()),
                 "ms_per_step": e2e_ms_max},
-        "gpu_launches": 2 * args.steps,
+        "prep": {"bound": "hbm", "kernels": "k_prep_iir_int (interior blocks) + k_prep_iir "
+                 "(record ends)", "ms": prep_ms, "bytes": prep_bytes,
+                 "achieved": prep_bytes / (prep_ms / 1e3) / 1e9, "peak": hbm_gbs,
+                 "unit": "GB/s", "frac": prep_bytes / (prep_ms / 1e3) / 1e9 / hbm_gbs,
+                 "peak_source": hbm_src},
+        # per step: the two prep kernels and the forward scatter
+        "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -28,7 +28,9 @@
  *    observers into its own device memory.  Buffers may be device pointers
  *    (used in place, on `stream`) or host pointers (pageable or pinned; the
  *    library stages them through device memory it owns and copies results
- *    back before returning).
+ *    back before returning).  Host inputs are read by copies that complete
+ *    before `stream` passes the call: with a device output the call may
+ *    return earlier, and the input must stay unchanged until then.
  *  - `stream` is a cudaStream_t passed as void* (NULL = default stream).
  *    Device work is enqueued on it; calls with host outputs synchronise it.
  *  - Every call returns a status and never aborts; fwh_last_error() gives a
@@ -93,7 +95,10 @@ fwh_status fwh_set_observers(fwh_handle h, int64_t n_obs, const double *xyz);
  * Forward pass: far-field pressure p_out [O][nt] (double) from the fields
  * [nt][5][P] (double for FWH_FP64, float for FWH_MIXED), nt >= 3.
  * Covers the "compute Noise", "compute t", "interp pressure signal" and
- * surface-integration stages (Sec. III B, III C).
+ * surface-integration stages (Sec. III B, III C).  Host FWH_MIXED fields of
+ * 256 frames or more are copied in 128-frame slabs on streams the handle owns,
+ * overlapped with the preparation and scatter of the frames already copied;
+ * the call still returns only when p_out holds the result.
  * Errors: FWH_ERR_STATE before fwh_set_observers, FWH_ERR_ARG for nt < 3,
  * null pointers, or (FWH_MIXED) n_panels x round_up(nt, 256) >= 2^32 (series
  * rows are addressed with 32-bit indices; checked before any work, the handle
@@ -153,7 +158,10 @@ fwh_status fwh_set_tile_config(fwh_handle h, int config);
  * while fwh_set_timing(h, 1) is on: [0] integrand preparation, [1] the
  * forward scatter kernel, [2] the whole call.  fwh_last_timings gives the
  * last call; fwh_timing_totals the sums over all timed calls since the last
- * reset and their count.  Both synchronise on the recorded events.
+ * reset and their count.  Both synchronise on the recorded events.  When a
+ * FWH_MIXED call takes host fields of 256 frames or more, the copy, the
+ * preparation and the scatter overlap in 128-frame slabs: [0] then runs to
+ * the start of the first scatter launch and [1] from there to the end.
  */
 fwh_status fwh_set_timing(fwh_handle h, int enable);
 fwh_status fwh_last_timings(fwh_handle h, float *ms3);

@@ -88,7 +88,8 @@ struct fwh_ctx {
   std::map<std::vector<uintptr_t>, BatchPlan> bplans;
   cudaStream_t side = nullptr;
   cudaStream_t copy = nullptr;              // host-field slabs (fwh_forward)
-  std::vector<cudaEvent_t> slab_ev;         // one per slab, plus the start
+  cudaStream_t pstream = nullptr;           // their series prep
+  std::vector<cudaEvent_t> slab_ev;         // per slab: copied, prepared; plus the start
   cudaEvent_t bev[2] = {nullptr, nullptr};
 };
 
@@ -300,11 +301,12 @@ fwh_status ensure_tmap(fwh_handle h, int box_rows) {
   return FWH_OK;
 }
 
-// Host fields of a mixed handle are copied in slabs of kSlab source frames on
-// a copy stream; the series of slab q are prepared as soon as slab q + 1 (which
-// holds the filters' reach beyond it) has landed, so the prep runs under the
-// copy of the later slabs and only the forward scatter waits for the last one.
-constexpr int kSlab = 256;
+// Host fields of a mixed handle are copied in slabs of kSlab source frames; the
+// series of slab q are prepared as soon as slab q + 1 (which holds the filters'
+// reach beyond it) has landed, and the forward scatter runs in segments of two
+// chunks, each as soon as its rows are prepared, so copy, prep and scatter
+// overlap and only the last slab's prep and segment follow the last copy.
+constexpr int kSlab = 128;
 
 template <typename T>
 fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStream_t s,
@@ -343,42 +345,6 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
   pa.ca = h->ca;
   pa.sa = h->sa;
   pa.dt = h->dt;
-  if (host_fields == nullptr) {
-    CK(h, launch_prep<T>(pa, s));
-  } else {
-    const int nslab = (int)((h->nt + kSlab - 1) / kSlab);
-    const size_t row = (size_t)5 * h->P * sizeof(T);
-    if (!h->copy) CK(h, cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking));
-    while ((int)h->slab_ev.size() < nslab + 1) {
-      cudaEvent_t e;
-      CK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-      h->slab_ev.push_back(e);
-    }
-    // the staging buffer is free once the work already on `s` is done
-    CK(h, cudaEventRecord(h->slab_ev[nslab], s));
-    CK(h, cudaStreamWaitEvent(h->copy, h->slab_ev[nslab], 0));
-    // copy slab q, then prepare slab q - 1, whose filter reach (83 frames)
-    // ends inside slab q; the last slab after the last copy.  Issuing them
-    // interleaved keeps the overlap when a pageable source makes each copy
-    // call return only after staging it.
-    constexpr int cps = kSlab / 64;  // 64-sample prep chunks per slab
-    for (int q = 0; q < nslab; ++q) {
-      const int64_t r0 = (int64_t)q * kSlab, r1 = std::min<int64_t>(h->nt, r0 + kSlab);
-      CK(h, cudaMemcpyAsync(const_cast<T *>(d_fields) + r0 * 5 * h->P,
-                            host_fields + r0 * 5 * h->P, (size_t)(r1 - r0) * row,
-                            cudaMemcpyHostToDevice, h->copy));
-      CK(h, cudaEventRecord(h->slab_ev[q], h->copy));
-      if (q == 0) continue;
-      CK(h, cudaStreamWaitEvent(s, h->slab_ev[q], 0));
-      pa.c_lo = (q - 1) * cps;
-      pa.c_hi = q * cps;
-      CK(h, launch_prep<T>(pa, s));
-    }
-    pa.c_lo = (nslab - 1) * cps;
-    pa.c_hi = h->ntp / 64;
-    CK(h, launch_prep<T>(pa, s));
-  }
-  if (tev) CK(h, cudaEventRecord(tev[1], s));
   FwdArgs<T> fa{};
   fa.tmX = h->tmap.p;
   fa.X = pa.X;
@@ -396,8 +362,73 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
   obs_tiling(h, c, &fa.obs_per_cta, &fa.n_obs_groups);
   fa.seg_len = c.seg_chunks * 32 * c.tk;
   fa.n_segs = (h->ntp + fa.seg_len - 1) / fa.seg_len;
+  fa.seg_lo = 0;
+  fa.seg_cnt = fa.n_segs;
   fa.win = c.win;
-  CK(h, launch_forward<T>(fa, cfg, s));
+  if (host_fields == nullptr) {
+    CK(h, launch_prep<T>(pa, s));
+    if (tev) CK(h, cudaEventRecord(tev[1], s));
+    CK(h, launch_forward<T>(fa, cfg, s));
+  } else {
+    // Three streams: `copy` moves the slabs, `prep` (high priority, so that
+    // its blocks get onto SMs between the scatter's) prepares slab q - 1 once
+    // slab q is in (the filters reach 83 frames past a slab), and `s` scatters
+    // each two-chunk time segment once all its rows are prepared.
+    // The copy stream first waits for the work already on `s` (the previous
+    // call's scatter reads X and its prep the staging buffer), so every later
+    // step of this call is ordered after it.
+    const int nslab = (int)((h->nt + kSlab - 1) / kSlab);
+    const size_t row = (size_t)5 * h->P * sizeof(T);
+    if (!h->copy) CK(h, cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking));
+    if (!h->pstream) {
+      int least = 0, greatest = 0;
+      CK(h, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+      CK(h, cudaStreamCreateWithPriority(&h->pstream, cudaStreamNonBlocking, greatest));
+    }
+    fa.seg_len = 2 * 32 * c.tk;
+    fa.n_segs = (h->ntp + fa.seg_len - 1) / fa.seg_len;
+    while ((int)h->slab_ev.size() < 2 * nslab + 1) {
+      cudaEvent_t e;
+      CK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      h->slab_ev.push_back(e);
+    }
+    cudaEvent_t *ev_in = h->slab_ev.data(), *ev_x = ev_in + nslab, ev_go = ev_in[2 * nslab];
+    CK(h, cudaEventRecord(ev_go, s));
+    CK(h, cudaStreamWaitEvent(h->copy, ev_go, 0));
+    constexpr int cps = kSlab / 64;  // 64-sample prep chunks per slab
+    static_assert(kSlab % 64 == 0 && 256 % kSlab == 0, "slabs tile the padded record");
+    int seg_done = 0;
+    // scatter the segments whose rows lie below rows_ready (prepared by slab j)
+    auto scatter_upto = [&](int rows_ready, int j) -> fwh_status {
+      const int ready = rows_ready >= h->ntp ? fa.n_segs : rows_ready / fa.seg_len;
+      if (ready <= seg_done) return FWH_OK;
+      CK(h, cudaStreamWaitEvent(s, ev_x[j], 0));
+      if (tev && seg_done == 0) CK(h, cudaEventRecord(tev[1], s));
+      fa.seg_lo = seg_done;
+      fa.seg_cnt = ready - seg_done;
+      CK(h, launch_forward<T>(fa, cfg, s));
+      seg_done = ready;
+      return FWH_OK;
+    };
+    for (int q = 0; q <= nslab; ++q) {
+      if (q < nslab) {
+        const int64_t r0 = (int64_t)q * kSlab, r1 = std::min<int64_t>(h->nt, r0 + kSlab);
+        CK(h, cudaMemcpyAsync(const_cast<T *>(d_fields) + r0 * 5 * h->P,
+                              host_fields + r0 * 5 * h->P, (size_t)(r1 - r0) * row,
+                              cudaMemcpyHostToDevice, h->copy));
+        CK(h, cudaEventRecord(ev_in[q], h->copy));
+      }
+      if (q == 0) continue;
+      const int j = q - 1;  // slab to prepare
+      CK(h, cudaStreamWaitEvent(h->pstream, ev_in[std::min(q, nslab - 1)], 0));
+      pa.c_lo = j * cps;
+      pa.c_hi = q < nslab ? q * cps : h->ntp / 64;
+      CK(h, launch_prep<T>(pa, h->pstream));
+      CK(h, cudaEventRecord(ev_x[j], h->pstream));
+      const fwh_status st1 = scatter_upto(pa.c_hi * 64, j);
+      if (st1 != FWH_OK) return st1;
+    }
+  }
   if (tev) CK(h, cudaEventRecord(tev[2], s));
   return FWH_OK;
 }
@@ -866,6 +897,7 @@ void fwh_destroy(fwh_handle h) {
     if (h->bev[i]) cudaEventDestroy(h->bev[i]);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->copy) cudaStreamDestroy(h->copy);
+  if (h->pstream) cudaStreamDestroy(h->pstream);
   for (cudaEvent_t e : h->slab_ev) cudaEventDestroy(e);
   delete h;
 }
@@ -919,6 +951,8 @@ fwh_status batch_build(int n, const fwh_handle *hs, const void *const *fields,
     obs_tiling(h, c, &fa.obs_per_cta, &fa.n_obs_groups);
     fa.seg_len = c.seg_chunks * 32 * c.tk;
     fa.n_segs = (h->ntp + fa.seg_len - 1) / fa.seg_len;
+    fa.seg_lo = 0;
+    fa.seg_cnt = fa.n_segs;
     fa.win = c.win;
     prefix[i + 1] = prefix[i] + fa.nsets * fa.n_obs_groups * fa.n_segs;
   }
@@ -1132,6 +1166,8 @@ fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, d
   obs_tiling(h, c, &fa.obs_per_cta, &fa.n_obs_groups);
   fa.seg_len = c.seg_chunks * 32 * c.tk;
   fa.n_segs = (ntp + fa.seg_len - 1) / fa.seg_len;
+  fa.seg_lo = 0;
+  fa.seg_cnt = fa.n_segs;
   fa.win = c.win;
   CK(h, launch_forward<T>(fa, cfg, s));
   return FWH_OK;

@@ -255,8 +255,8 @@ struct Item {
     // last CTAs to start are the shortest
     const int g = item % ng;
     const int rest = item / ng;
-    const int q = rest % a.n_segs;
-    const int r2 = rest / a.n_segs;
+    const int q = a.seg_lo + rest % a.seg_cnt;
+    const int r2 = rest / a.seg_cnt;
     sidx = a.set_order ? a.set_order[r2] : r2;
     p_begin = a.set_begin[sidx];
     p_end = a.set_begin[sidx + 1];
@@ -979,7 +979,8 @@ cudaError_t launch_one(const FwdArgs<T> &a, const FwdConfig &c, cudaStream_t s) 
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  const int items = a.nsets * a.n_obs_groups * a.n_segs;
+  if (a.seg_lo < 0 || a.seg_cnt < 1 || a.seg_lo + a.seg_cnt > a.n_segs) return cudaErrorInvalidValue;
+  const int items = a.nsets * a.n_obs_groups * a.seg_cnt;
   if (items <= 0) return cudaSuccess;
   kern<<<items, cta_threads<NW, PIPE>(), smem, s>>>(a, c.stages);
   return cudaGetLastError();

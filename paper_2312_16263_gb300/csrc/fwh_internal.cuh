@@ -71,6 +71,7 @@ struct PrepArgs {
   int P, nt, ntp, chunk;
   double ca, sa, dt;
   int c_lo, c_hi;       // FP32: 64-sample chunks [c_lo, c_hi) to prepare (0, 0: all)
+  int int_lo, int_hi;   // FP32, set by the launcher: the interior chunks within [c_lo, c_hi)
 };
 
 template <typename T>
@@ -87,6 +88,7 @@ struct FwdArgs {
   int nsets, O, ntp, nt;
   int obs_per_cta, n_obs_groups;
   int seg_len, n_segs;
+  int seg_lo, seg_cnt;  // this launch covers time segments [seg_lo, seg_lo + seg_cnt)
   int win;              // window slots per observer
 };
 

@@ -24,6 +24,8 @@
 // per 32-sample block (see the kernel), written as whole X tiles.
 #include "fwh_internal.cuh"
 
+#include <algorithm>
+
 #include <cstdint>
 
 namespace fwh {
@@ -267,17 +269,18 @@ __global__ void __launch_bounds__(PrepTile<T>::panels * 8) k_prep(PrepArgs<T> a)
 // applied to the extended r.  That inverse factors as
 //   m = -rho (1 - rho z)^-1 (1 - rho z^-1)^-1 r,   rho = sqrt(3) - 2,
 // a causal recursion y_k = r_k + rho y_{k-1} followed by an anti-causal one
-// x_k = y_k + rho x_{k+1}, m_k = -rho x_k.  Each thread filters 32 samples,
-// starting both recursions H samples outside its block (error |rho|^H, below
-// FP32 rounding for H = 16), so every sample block is independent: no
-// sequential sweep over the window, no intermediate values in HBM.
+// x_k = y_k + rho x_{k+1}, m_k = -rho x_k.  Both recursions start H samples
+// outside the 64-sample block they serve (error |rho|^H, below FP32 rounding
+// for H = 16), so every block is independent: no sequential sweep over the
+// record, no intermediate values in HBM.
 //
-// CTA tile: 16 panels x 64 samples (one 64-sample block of the FP32 rows);
-// thread (half, panel, series) filters samples [32 half, 32 half + 32) of the
-// tile.  Phase A stages the four integrands of the rows the filters reach
-// (folded back into the record), phase B filters into a shared copy of the
-// tile in the row layout of X, phase C writes the tile with coalesced 16-byte
-// stores (4 KB contiguous per panel).
+// Two kernels share the blocks of a record:
+//  * k_prep_iir_int, the interior blocks (filter reach inside rows 1..N-2):
+//    persistent CTAs walk consecutive blocks of one 16-panel group, with the
+//    field rows of the next block in flight (cp.async) while the current one
+//    is filtered;
+//  * k_prep_iir, the blocks at the record ends (the odd-periodic extension
+//    and the one-sided end differences) and the empty blocks past nt.
 // ---------------------------------------------------------------------------
 constexpr int kIirPanels = 8;
 constexpr int kIirChunk = 64;
@@ -288,159 +291,375 @@ constexpr int kIirRows = kIirChunk + 2 * kIirH + 6;  // bound on the staged rows
 constexpr int kIirQ = 8;  // integrand stride in a staged row (4 integrands x 4 panels of a warp: distinct banks)
 constexpr int kIirRow = 4 * kIirQ;                   // staged row stride (floats)
 
-__global__ void __launch_bounds__(kIirThreads, 4) k_prep_iir(PrepArgs<float> a) {
+// ---------------------------------------------------------------------------
+// FP32 prep of the interior blocks.  Away from the record ends the moment
+// solve and the central time difference are both convolutions, so they
+// commute: the moments of a derivative series are the central differences of
+// the moments of its value series, m'_k = (m_{k+1} - m_{k-1}) / (2 dt).  Only
+// the four value series are filtered, and one thread owns one (panel,
+// integrand) over a whole 64-sample block; the four threads of a panel
+// assemble each half row of X (samples r and 32 + r of eight slots) and store
+// it as four 16-byte pieces.  Blocks whose filter reach touches a record end
+// are left to k_prep_iir.
+// ---------------------------------------------------------------------------
+constexpr int kIntPanels = 16;
+constexpr int kIntThreads = kIntPanels * 4;
+constexpr int kIntRow = kIntPanels * 4;              // staged row: [panel][integrand]
+constexpr int kIntRows = kIirChunk + 2 * kIirH + 4;  // samples c0 - H - 3 .. c0 + 64 + H
+constexpr int kIntKeep = kIntRows - kIirChunk;       // rows shared by consecutive blocks
+constexpr int kIntUnit = 8;                          // blocks per work unit
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = ok ? 4 : 0;  // zero fill
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kIntThreads, 4) k_prep_iir_int(PrepArgs<float> a) {
+  constexpr int NP = kIntPanels, H = kIirH, C = kIirChunk;
+  constexpr float rho = -0.267949192431122706f;  // sqrt(3) - 2
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *sb = reinterpret_cast<float *>(smem_raw);  // [kIntRows][NP][4] integrands
+  float *raw = sb + kIntRows * kIntRow;             // [C rows][5][NP] fields in flight
+  const int tid = threadIdx.x;
+  const int n_pg = (a.P + NP - 1) / NP;
+  const int n_blk = a.int_hi - a.int_lo;
+  const int n_us = (n_blk + kIntUnit - 1) / kIntUnit;
+  const long n_units = (long)n_pg * n_us;
+  // phase A thread: panel pa, rows tid / NP + 4 u
+  const int pa = tid % NP;
+  // phase B thread: integrand qi of panel pl
+  const int qi = tid & 3;
+  const int pl = tid >> 2;
+  const bool q_lo2 = qi < 2, q_is1 = qi == 1, q_is2 = qi == 2;  // lane role in put_row
+  const float inv2h = (float)(0.5 / a.dt);
+  const float s6 = (float)(6.0 / (a.dt * a.dt));
+  const bool vec = a.perm == nullptr && (a.P & 3) == 0 &&
+                   ((size_t)a.fields & 15) == 0;  // 16-byte copies of 4 panels
+  for (long u = blockIdx.x; u < n_units; u += gridDim.x) {
+    // panel group fastest: concurrent units read neighbouring segments of the same rows
+    const int p0 = (int)(u % n_pg) * NP;
+    const int b0 = a.int_lo + (int)(u / n_pg) * kIntUnit;
+    const int b1 = min(a.int_lo + n_blk, b0 + kIntUnit);
+    const int p = p0 + pa;
+    const bool live = p < a.P;
+    float n0 = 0.f, n1 = 0.f, n2 = 0.f, Un = 0.f;
+    if (live) {
+      n0 = (float)a.n[3 * p];
+      n1 = (float)a.n[3 * p + 1];
+      n2 = (float)a.n[3 * p + 2];
+      Un = (float)(a.ca * a.n[3 * p] + a.sa * a.n[3 * p + 1]);
+    }
+    const int pb = p0 + pl;
+    const bool live_b = pb < a.P;
+    // copy field rows [r0, r0 + n) of the group into raw (n <= C)
+    auto issue = [&](int r0, int n) {
+      if (vec) {
+        for (int e = tid; e < n * 5 * (NP / 4); e += kIntThreads) {
+          const int q4 = e % (NP / 4), rc = e / (NP / 4);  // rc = row * 5 + component
+          const int pq = p0 + 4 * q4;
+          if (pq < a.P)
+            cp_async16(raw + rc * NP + 4 * q4, a.fields + ((size_t)(r0 * 5) + rc) * a.P + pq);
+          else
+            *reinterpret_cast<float4 *>(raw + rc * NP + 4 * q4) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      } else {
+        const int po = live ? (a.perm ? a.perm[p] : p) : 0;
+        for (int rc = tid / NP; rc < n * 5; rc += kIntThreads / NP)
+          cp_async4(raw + rc * NP + pa, a.fields + ((size_t)(r0 * 5) + rc) * a.P + po, live);
+      }
+    };
+    // integrands of the n rows in raw into window rows [w0, w0 + n)
+    auto integrands = [&](int w0, int n) {
+      for (int r = tid / NP; r < n; r += kIntThreads / NP) {
+        const float *f = raw + r * 5 * NP + pa;
+        const float rho_ = f[0], u0v = f[NP], u1 = f[2 * NP], u2 = f[3 * NP], pp = f[4 * NP];
+        const float un = u0v * n0 + u1 * n1 + u2 * n2;
+        const float r1 = 1.f + rho_;
+        const float utn = Un + un;
+        float4 q;
+        q.x = rho_ * Un + r1 * un;             // Qn   (Eq. Qn_New_nd)
+        q.y = pp * n0 + r1 * u0v * utn;        // L_1  (Eq. Li_New_nd)
+        q.z = pp * n1 + r1 * u1 * utn;
+        q.w = pp * n2 + r1 * u2 * utn;
+        *reinterpret_cast<float4 *>(sb + (size_t)(w0 + r) * kIntRow + pa * 4) = q;
+      }
+    };
+    // window of block b: rows c0 - H - 3 .. c0 + C + H; load its first C rows,
+    // then the rest, so that later blocks only add C rows each
+    {
+      const int lo = b0 * C - H - 3;
+      __syncthreads();  // the previous unit is done with raw and sb
+      issue(lo, C);
+      cp_async_wait_all();
+      __syncthreads();
+      integrands(0, C);
+      __syncthreads();
+      issue(lo + C, kIntKeep);
+      cp_async_wait_all();
+      __syncthreads();
+      integrands(C, kIntKeep);
+      __syncthreads();
+    }
+    for (int b = b0; b < b1; ++b) {
+      const int c0 = b * C;
+      const bool more = b + 1 < b1;
+      if (more) issue(c0 + C + H + 1, C);  // rows of the next window, in flight meanwhile
+      // ---- phase B: filters of block b ----------------------------------------
+      float *xr = a.X + ((size_t)(live_b ? pb : 0) * a.ntp + c0) * kRec;
+      // one half row (slots q0 .. q0 + 7 of row r) from the four lanes of a
+      // panel: lane qi stores slots q0 + 2 qi, q0 + 2 qi + 1 as one float4 after
+      // taking its neighbours' pairs (slot order: d0 v0 d1 d2 | d3 v1 v2 v3)
+      auto put_row = [&](int r, int q0, float dl, float dh, float vl, float vh) {
+        const float xl = __shfl_down_sync(0xffffffffu, dl, 1);
+        const float xh = __shfl_down_sync(0xffffffffu, dh, 1);
+        const float yl = __shfl_up_sync(0xffffffffu, vl, 1);
+        const float yh = __shfl_up_sync(0xffffffffu, vh, 1);
+        const float4 o = make_float4(q_lo2 ? dl : (q_is2 ? xl : yl), q_lo2 ? dh : (q_is2 ? xh : yh),
+                                     q_is1 ? xl : (q_is2 ? yl : vl), q_is1 ? xh : (q_is2 ? yh : vh));
+        if (live_b) *reinterpret_cast<float4 *>(xr + r * 2 * kRec + (q0 + 2 * qi) * 2) = o;
+      };
+      const float *bc = sb + (size_t)(H + 3) * kIntRow + pl * 4 + qi;
+      auto B = [&](int k) -> float { return bc[k * kIntRow]; };  // k relative to c0
+      float y[C + H + 1];
+      float yy = 0.f;
+      float Bm = B(-2 - H), B0 = B(-1 - H);
+#pragma unroll
+      for (int k = -1 - H; k <= C + H - 1; ++k) {
+        const float Bp = B(k + 1);
+        yy = s6 * (Bp - 2.f * B0 + Bm) + rho * yy;
+        if (k >= -1) y[k + 1] = yy;
+        if (k >= C / 2 && k < C) {  // series pairs (k - 32, k)
+          const int r = k - C / 2;
+          put_row(r, 0, (B(r + 1) - B(r - 1)) * inv2h, (Bp - Bm) * inv2h, B(r), B0);
+        }
+        Bm = B0;
+        B0 = Bp;
+      }
+      float mh[C / 2 + 2];  // m_k for k = C/2 - 1 .. C
+      float xx = 0.f, m1 = 0.f, m2 = 0.f;
+#pragma unroll
+      for (int k = C + H - 1; k >= -1; --k) {
+        xx = y[k + 1] + rho * xx;
+        const float mk = -rho * xx;
+        if (k >= C / 2 - 1 && k <= C) mh[k - (C / 2 - 1)] = mk;
+        if (k <= C / 2 - 2) {  // moment pairs of row r = k + 1
+          const int r = k + 1;
+          put_row(r, 8, (m2 - mk) * inv2h, (mh[r + 2] - mh[r]) * inv2h, m1, mh[r + 1]);
+        }
+        m2 = m1;
+        m1 = mk;
+      }
+      if (!more) break;
+      // ---- slide the window by C rows and add the rows now in raw --------------
+      __syncthreads();  // every thread is done reading the window
+      for (int e = tid; e < kIntKeep * kIntRow / 4; e += kIntThreads)
+        reinterpret_cast<float4 *>(sb)[e] = reinterpret_cast<const float4 *>(sb + C * kIntRow)[e];
+      cp_async_wait_all();
+      __syncthreads();
+      integrands(kIntKeep, C);
+      __syncthreads();
+    }
+  }
+}
+
+// General FP32 prep of a 64-sample block (used for the record ends): thread
+// (series, half, panel) filters 32 samples of one of the eight series; the
+// two halves of a (panel, series) are lanes 8 apart and store float2 pairs.
+__global__ void __launch_bounds__(kIirThreads, 6) k_prep_iir(PrepArgs<float> a) {
   constexpr int NP = kIirPanels, H = kIirH, J = kIirJ;
   constexpr float rho = -0.267949192431122706f;  // sqrt(3) - 2
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // tile [NP][32 rows][16][2] (16-byte chunk index of odd panels XOR 4, so
-  // that the four panels of a warp spread over the banks), then the staged
-  // integrands [rows][4 (stride kIirQ)][NP]
-  float *tile = reinterpret_cast<float *>(smem_raw);
-  float *sb = tile + NP * kIirChunk * kRec;
+  // staged integrands, two copies [rows][4 (stride kIirQ)][NP]: the second
+  // with its columns rotated by two, read by the threads of the upper half
+  // block (rows 32 apart would otherwise share a bank)
+  float *sb = reinterpret_cast<float *>(smem_raw);
+  float *sb2 = sb + kIirRows * kIirRow;
   const int tid = threadIdx.x;
-  const int n_ct = a.c_hi - a.c_lo;  // 1D grid: chunk fastest, then panel tile
-  const int c0 = (a.c_lo + (int)(blockIdx.x % n_ct)) * kIirChunk;
-  const int p0 = (int)(blockIdx.x / n_ct) * NP;
+  // 1D grid over the record-end chunks (fastest), then panel tiles
+  // 1D grid over the chunks of [c_lo, c_hi) outside [int_lo, int_hi) (fastest),
+  // then panel tiles
+  const int na = a.int_lo - a.c_lo, n_edge = na + a.c_hi - a.int_hi;
+  const int ei = (int)(blockIdx.x % n_edge);
+  const int c0 = (ei < na ? a.c_lo + ei : a.int_hi + ei - na) * kIirChunk;
+  const int p0 = (int)(blockIdx.x / n_edge) * NP;
   const int N = a.nt;
-  if (c0 < N) {
-    // staged integrand rows: the tile's filter reach plus FD neighbours, and
-    // for a tile at the record end the rows its window folds back onto
-    const int reach_lo = c0 - H - 3, reach_hi = c0 + kIirChunk + H + 3;
-    const int lo = max(0, min(reach_lo, 2 * (N - 1) - reach_hi));
-    const int hi = min(N, reach_hi);
-    // ---- phase A: integrands ----------------------------------------------
-    {
-      const int pl = tid % NP;
-      const int p = p0 + pl;
-      const bool live = p < a.P;
-      const int po = live ? (a.perm ? a.perm[p] : p) : 0;
-      float n0 = 0.f, n1 = 0.f, n2 = 0.f, Un = 0.f;
-      if (live) {
-        n0 = (float)a.n[3 * p];
-        n1 = (float)a.n[3 * p + 1];
-        n2 = (float)a.n[3 * p + 2];
-        Un = (float)(a.ca * a.n[3 * p] + a.sa * a.n[3 * p + 1]);
-      }
-      // all field loads of this thread's rows first, then the integrands
-      constexpr int RS = kIirThreads / NP;               // row stride between passes
-      constexpr int RPT = (kIirRows + RS - 1) / RS;      // passes
-      float fv[RPT][5];
-#pragma unroll
-      for (int u = 0; u < RPT; ++u) {
-        const int i = lo + tid / NP + u * RS;
-        const bool ok = live && i < hi;
-        const float *b = a.fields + (size_t)(ok ? i : 0) * 5 * a.P + po;
-#pragma unroll
-        for (int c = 0; c < 5; ++c) fv[u][c] = ok ? b[(size_t)c * a.P] : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < RPT; ++u) {
-        const int i = lo + tid / NP + u * RS;
-        if (i >= hi) break;
-        const float rho_ = fv[u][0], u0 = fv[u][1], u1 = fv[u][2], u2 = fv[u][3], pp = fv[u][4];
-        const float un = u0 * n0 + u1 * n1 + u2 * n2;
-        const float r1 = 1.f + rho_;
-        const float utn = Un + un;
-        float *row = sb + (size_t)(i - lo) * kIirRow + pl;
-        row[0] = rho_ * Un + r1 * un;                // Qn   (Eq. Qn_New_nd)
-        row[kIirQ] = pp * n0 + r1 * u0 * utn;        // L_1  (Eq. Li_New_nd)
-        row[2 * kIirQ] = pp * n1 + r1 * u1 * utn;
-        row[3 * kIirQ] = pp * n2 + r1 * u2 * utn;
-      }
+  // phase B thread: series s, half h (samples c0 + 32 h ..), panel pl; the
+  // two halves of a (panel, series) are lanes 8 apart of one warp
+  const int s = tid & 7;
+  const int h = (tid >> 3) & 1;
+  const int pl = tid >> 4;
+  const int pb = p0 + pl;
+  const bool live_b = pb < a.P;
+  // X rows of the tile: row r holds samples c0 + r and c0 + 32 + r
+  float *xr = a.X + ((size_t)(live_b ? pb : 0) * a.ntp + c0) * kRec;
+  // lane pair (h = 0, h = 1) stores one float2 {sample c0 + r, c0 + 32 + r}
+  // of slot q: the lower half for the series, the upper for the moments
+  auto put2 = [&](int r, int q, float v, bool mine) {
+    const float o = __shfl_xor_sync(0xffffffffu, v, 8);
+    if (mine && live_b)
+      *reinterpret_cast<float2 *>(xr + r * 2 * kRec + q * 2) =
+          h == 0 ? make_float2(v, o) : make_float2(o, v);
+  };
+  if (c0 >= N) {
+    for (int r = 0; r < J; ++r) {
+      put2(r, s, 0.f, h == 0);
+      put2(r, 8 + s, 0.f, h == 1);
     }
-    __syncthreads();
-    // ---- phase B: series and moments ----------------------------------------
-    const int s = tid & 7;
-    const int pl = (tid >> 3) % NP;
-    const int h = tid / (8 * NP);
-    const int ks = c0 + J * h;
-    const bool deriv = (s == 0) || (s >= 2 && s <= 4);
-    const int qi = (s <= 1) ? 0 : 1 + (s - 2) % 3;
-    const float *col = sb + qi * kIirQ + pl - (size_t)lo * kIirRow;  // B(i) = col[i * kIirRow]
-    const float inv2h = (float)(0.5 / a.dt);
-    const float s6 = (float)(6.0 / (a.dt * a.dt));
-    // interior series sample F_i = fa B(i+1) + fb B(i) + fc B(i-1)
-    const float fa = deriv ? inv2h : 0.f, fb = deriv ? 0.f : 1.f, fc = -fa;
-    auto B = [&](int i) -> float { return col[(size_t)i * kIirRow]; };
-    float *tp = tile + (size_t)pl * kIirChunk * kRec;
-    const int swz = (pl & 1) << 4;
-    auto put = [&](int t, int q, float v) { tp[(((t * kRec + q) * 2) + h) ^ swz] = v; };
-    const bool interior = ks - H - 1 >= 1 && ks + J + H <= N - 2;
-    if (interior) {
-      float y[J + H];
-      int k = ks - H;
-      float Bk = B(k), Bk1 = B(k + 1);
-      const float Bkm = B(k - 1);
-      float Fm = fa * Bk + fb * Bkm + fc * B(k - 2);   // F_{k-1}
-      float F0 = fa * Bk1 + fb * Bk + fc * Bkm;        // F_k
-      float yy = 0.f;
-#pragma unroll
-      for (int t = 0; t < J + 2 * H; ++t, ++k) {
-        const float Bk2 = B(k + 2);
-        const float Fp = fa * Bk2 + fb * Bk1 + fc * Bk;  // F_{k+1}
-        yy = s6 * (Fp - 2.f * F0 + Fm) + rho * yy;
-        if (t >= H) y[t - H] = yy;
-        if (t >= H && t < H + J) put(t - H, s, F0);
-        Bk = Bk1;
-        Bk1 = Bk2;
-        Fm = F0;
-        F0 = Fp;
-      }
-      float xx = 0.f;
-#pragma unroll
-      for (int t = J + H - 1; t >= 0; --t) {
-        xx = y[t] + rho * xx;
-        if (t < J) put(t, 8 + s, -rho * xx);
-      }
-    } else {
-      // record ends (few tiles, compact code): one-sided derivatives at the
-      // first and last frame, r on the odd-periodic extension
-      auto F = [&](int i) -> float {
-        if (!deriv) return B(i);
-        if (i == 0) return (-3.f * B(0) + 4.f * B(1) - B(2)) * inv2h;
-        if (i == N - 1) return (3.f * B(N - 1) - 4.f * B(N - 2) + B(N - 3)) * inv2h;
-        return (B(i + 1) - B(i - 1)) * inv2h;
-      };
-      const int L2 = 2 * (N - 1);
-      auto r_at = [&](int kk) -> float {
-        int km = kk % L2;
-        if (km < 0) km += L2;
-        float sg = 1.f;
-        if (km >= N - 1) {
-          km = L2 - km;
-          sg = -1.f;
-        }
-        if (km == 0 || km == N - 1) return 0.f;
-        return sg * s6 * (F(km + 1) - 2.f * F(km) + F(km - 1));
-      };
-      float ye[J + H];
-      float yy = 0.f;
-#pragma unroll 1
-      for (int t = 0; t < J + 2 * H; ++t) {
-        yy = r_at(ks - H + t) + rho * yy;
-        if (t >= H) ye[t - H] = yy;
-      }
-#pragma unroll 1
-      for (int t = 0; t < J; ++t) put(t, s, ks + t < N ? F(ks + t) : 0.f);
-      float xx = 0.f;
-#pragma unroll 1
-      for (int t = J + H - 1; t >= 0; --t) {
-        xx = ye[t] + rho * xx;
-        if (t < J) put(t, 8 + s, ks + t < N ? -rho * xx : 0.f);
-      }
+    return;
+  }
+  // staged integrand rows: the tile's filter reach plus FD neighbours, and
+  // for a tile at the record end the rows its window folds back onto
+  const int reach_lo = c0 - H - 3, reach_hi = c0 + kIirChunk + H + 3;
+  const int lo = max(0, min(reach_lo, 2 * (N - 1) - reach_hi));
+  const int hi = min(N, reach_hi);
+  // ---- phase A: integrands ------------------------------------------------
+  {
+    const int pl_a = tid % NP;
+    const int p = p0 + pl_a;
+    const bool live = p < a.P;
+    const int po = live ? (a.perm ? a.perm[p] : p) : 0;
+    float n0 = 0.f, n1 = 0.f, n2 = 0.f, Un = 0.f;
+    if (live) {
+      n0 = (float)a.n[3 * p];
+      n1 = (float)a.n[3 * p + 1];
+      n2 = (float)a.n[3 * p + 2];
+      Un = (float)(a.ca * a.n[3 * p] + a.sa * a.n[3 * p + 1]);
     }
-  } else {
-    for (int idx = tid; idx < NP * kIirChunk * kRec; idx += kIirThreads) tile[idx] = 0.f;
+    // all field loads of this thread's rows first, then the integrands
+    constexpr int RS = kIirThreads / NP;               // row stride between passes
+    constexpr int RPT = (kIirRows + RS - 1) / RS;      // passes
+    float fv[RPT][5];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      const int i = lo + tid / NP + u * RS;
+      const bool ok = live && i < hi;
+      const float *b = a.fields + (size_t)(ok ? i : 0) * 5 * a.P + po;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) fv[u][c] = ok ? b[(size_t)c * a.P] : 0.f;
+    }
+    const int rot = (pl_a + 2) & (NP - 1);
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      const int i = lo + tid / NP + u * RS;
+      if (i >= hi) break;
+      const float rho_ = fv[u][0], u0 = fv[u][1], u1 = fv[u][2], u2 = fv[u][3], pp = fv[u][4];
+      const float un = u0 * n0 + u1 * n1 + u2 * n2;
+      const float r1 = 1.f + rho_;
+      const float utn = Un + un;
+      const float q0 = rho_ * Un + r1 * un;            // Qn   (Eq. Qn_New_nd)
+      const float q1 = pp * n0 + r1 * u0 * utn;        // L_1  (Eq. Li_New_nd)
+      const float q2 = pp * n1 + r1 * u1 * utn;
+      const float q3 = pp * n2 + r1 * u2 * utn;
+      float *row = sb + (size_t)(i - lo) * kIirRow;
+      float *row2 = sb2 + (size_t)(i - lo) * kIirRow;
+      row[pl_a] = q0;
+      row[kIirQ + pl_a] = q1;
+      row[2 * kIirQ + pl_a] = q2;
+      row[3 * kIirQ + pl_a] = q3;
+      row2[rot] = q0;
+      row2[kIirQ + rot] = q1;
+      row2[2 * kIirQ + rot] = q2;
+      row2[3 * kIirQ + rot] = q3;
+    }
   }
   __syncthreads();
-  // ---- phase C: tile -> X (16-byte chunks, un-swizzled) ------------------------
-  constexpr int V4 = kIirChunk * kRec / 4;  // float4 per panel
-  for (int idx = tid; idx < NP * V4; idx += kIirThreads) {
-    const int pl = idx / V4, v = idx % V4;
-    const int p = p0 + pl;
-    if (p < a.P)
-      reinterpret_cast<float4 *>(a.X + ((size_t)p * a.ntp + c0) * kRec)[v] =
-          reinterpret_cast<const float4 *>(tile)[pl * V4 + (v ^ ((pl & 1) << 2))];
+  // ---- phase B: series and moments, stored straight to X ---------------------
+  const int ks = c0 + J * h;
+  const bool deriv = (s == 0) || (s >= 2 && s <= 4);
+  const int qi = (s <= 1) ? 0 : 1 + (s - 2) % 3;
+  const float *col = (h ? sb2 + ((pl + 2) & (NP - 1)) : sb + pl) + qi * kIirQ -
+                     (size_t)lo * kIirRow;  // B(i) = col[i * kIirRow]
+  const float inv2h = (float)(0.5 / a.dt);
+  const float s6 = (float)(6.0 / (a.dt * a.dt));
+  auto B = [&](int i) -> float { return col[(size_t)i * kIirRow]; };
+  // (each path is taken by the whole CTA, so that the pair exchange in put2
+  // runs on full warps)
+  // Records of 82 frames or more: every index the filters reach folds back
+  // into the record with one reflection, and the odd-periodic extension of r
+  // is the second difference of the series point-reflected about its end
+  // values, F(-k) = 2 F(0) - F(k), F(N - 1 + k) = 2 F(N - 1) - F(N - 1 - k)
+  // (r then also vanishes at both ends).  So the filters run on that
+  // extension with the same unrolled recursion as the interior.
+  if (N >= 82) {
+    float Fs = 0.f, Fe = 0.f;  // series at the first and last frame (one-sided derivatives)
+    if (lo == 0) Fs = deriv ? (-3.f * B(0) + 4.f * B(1) - B(2)) * inv2h : B(0);
+    if (hi == N) Fe = deriv ? (3.f * B(N - 1) - 4.f * B(N - 2) + B(N - 3)) * inv2h : B(N - 1);
+    auto Fx = [&](int kk) -> float {
+      const bool neg = kk < 0, big = kk > N - 1;
+      const int m = neg ? -kk : (big ? 2 * (N - 1) - kk : kk);
+      float v;
+      if (deriv) {
+        const float c = (B(min(m + 1, N - 1)) - B(max(m - 1, 0))) * inv2h;
+        v = m == 0 ? Fs : (m == N - 1 ? Fe : c);
+      } else {
+        v = B(m);
+      }
+      return neg ? 2.f * Fs - v : (big ? 2.f * Fe - v : v);
+    };
+    float y[J + H];
+    int k = ks - H;
+    float Fm = Fx(k - 1), F0 = Fx(k);
+    float yy = 0.f;
+#pragma unroll
+    for (int t = 0; t < J + 2 * H; ++t, ++k) {
+      const float Fp = Fx(k + 1);
+      yy = s6 * (Fp - 2.f * F0 + Fm) + rho * yy;
+      if (t >= H) y[t - H] = yy;
+      if (t >= H && t < H + J) put2(t - H, s, k < N ? F0 : 0.f, h == 0);
+      Fm = F0;
+      F0 = Fp;
+    }
+    float xx = 0.f;
+#pragma unroll
+    for (int t = J + H - 1; t >= 0; --t) {
+      xx = y[t] + rho * xx;
+      if (t < J) put2(t, 8 + s, ks + t < N ? -rho * xx : 0.f, h == 1);
+    }
+  } else {
+    // short records (compact code): one-sided derivatives at the first and
+    // last frame, r on the odd-periodic extension of any number of periods
+    auto F = [&](int i) -> float {
+      if (!deriv) return B(i);
+      if (i == 0) return (-3.f * B(0) + 4.f * B(1) - B(2)) * inv2h;
+      if (i == N - 1) return (3.f * B(N - 1) - 4.f * B(N - 2) + B(N - 3)) * inv2h;
+      return (B(i + 1) - B(i - 1)) * inv2h;
+    };
+    const int L2 = 2 * (N - 1);
+    auto r_at = [&](int kk) -> float {
+      int km = kk % L2;
+      if (km < 0) km += L2;
+      float sg = 1.f;
+      if (km >= N - 1) {
+        km = L2 - km;
+        sg = -1.f;
+      }
+      if (km == 0 || km == N - 1) return 0.f;
+      return sg * s6 * (F(km + 1) - 2.f * F(km) + F(km - 1));
+    };
+    float ye[J + H];
+    float yy = 0.f;
+#pragma unroll 1
+    for (int t = 0; t < J + 2 * H; ++t) {
+      yy = r_at(ks - H + t) + rho * yy;
+      if (t >= H) ye[t - H] = yy;
+    }
+#pragma unroll 1
+    for (int t = 0; t < J; ++t) put2(t, s, ks + t < N ? F(ks + t) : 0.f, h == 0);
+    float xx = 0.f;
+#pragma unroll 1
+    for (int t = J + H - 1; t >= 0; --t) {
+      xx = ye[t] + rho * xx;
+      if (t < J) put2(t, 8 + s, ks + t < N ? -rho * xx : 0.f, h == 1);
+    }
   }
 }
 
@@ -725,12 +944,6 @@ __global__ void __launch_bounds__(kIirThreads) k_prep_adj_iir(PrepAdjArgs<float>
 template <typename T>
 cudaError_t launch_prep(const PrepArgs<T> &a0, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    // tile + staged integrand rows
-    const size_t smem =
-        ((size_t)kIirPanels * kIirChunk * kRec + (size_t)kIirRows * kIirRow) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_prep_iir, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
     if (a0.ntp % kIirChunk != 0) return cudaErrorInvalidValue;
     PrepArgs<float> a = a0;
     if (a.c_hi == 0) {
@@ -738,9 +951,41 @@ cudaError_t launch_prep(const PrepArgs<T> &a0, cudaStream_t s) {
       a.c_hi = a.ntp / kIirChunk;
     }
     if (a.c_lo < 0 || a.c_hi > a.ntp / kIirChunk || a.c_lo >= a.c_hi) return cudaErrorInvalidValue;
-    const long blocks = (long)(a.c_hi - a.c_lo) * ((a.P + kIirPanels - 1) / kIirPanels);
-    if (blocks > INT32_MAX) return cudaErrorInvalidValue;
-    k_prep_iir<<<(unsigned)blocks, kIirThreads, smem, s>>>(a);
+    // interior blocks: filter reach inside rows 1 .. N - 2 (c0 >= H + 2 and
+    // c0 + C + H + 1 <= N), by the persistent kernel
+    const int last_int = a.nt >= kIirChunk + kIirH + 1 ? (a.nt - kIirChunk - kIirH - 1) / kIirChunk : -1;
+    a.int_lo = std::max(a.c_lo, (kIirH + 2 + kIirChunk - 1) / kIirChunk);
+    a.int_hi = std::min(a.c_hi, last_int + 1);
+    if (a.int_lo >= a.int_hi) a.int_lo = a.int_hi = a.c_hi;
+    cudaError_t e;
+    if (a.int_hi > a.int_lo) {
+      const size_t smem_i = ((size_t)kIntRows * kIntRow + (size_t)kIirChunk * 5 * kIntPanels) *
+                            sizeof(float);
+      e = cudaFuncSetAttribute(k_prep_iir_int, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_i);
+      if (e != cudaSuccess) return e;
+      int dev = 0, sms = 0, per_sm = 0;
+      if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+      if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prep_iir_int, kIntThreads,
+                                                             smem_i)) != cudaSuccess)
+        return e;
+      const long units = (long)((a.P + kIntPanels - 1) / kIntPanels) *
+                         ((a.int_hi - a.int_lo + kIntUnit - 1) / kIntUnit);
+      const long grid = std::min<long>(units, (long)std::max(per_sm, 1) * sms);
+      k_prep_iir_int<<<(unsigned)grid, kIntThreads, smem_i, s>>>(a);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // record-end and empty blocks by the general kernel
+    const int n_edge = (a.int_lo - a.c_lo) + (a.c_hi - a.int_hi);
+    if (n_edge == 0) return cudaSuccess;
+    const size_t smem = (size_t)2 * kIirRows * kIirRow * sizeof(float);
+    e = cudaFuncSetAttribute(k_prep_iir, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long eblocks = (long)n_edge * ((a.P + kIirPanels - 1) / kIirPanels);
+    if (eblocks > INT32_MAX) return cudaErrorInvalidValue;
+    k_prep_iir<<<(unsigned)eblocks, kIirThreads, smem, s>>>(a);
     return cudaGetLastError();
   } else {
     constexpr int NP = PrepTile<T>::panels;
