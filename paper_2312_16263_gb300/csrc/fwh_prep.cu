@@ -281,6 +281,7 @@ __global__ void __launch_bounds__(PrepTile<T>::panels * 8) k_prep(PrepArgs<T> a)
 //    is filtered;
 //  * k_prep_iir, the blocks at the record ends (the odd-periodic extension
 //    and the one-sided end differences) and the empty blocks past nt.
+// The FP32 adjoint k_prep_adj_iir below shares the tile constants.
 // ---------------------------------------------------------------------------
 constexpr int kIirPanels = 8;
 constexpr int kIirChunk = 64;
@@ -288,7 +289,7 @@ constexpr int kIirJ = 32;
 constexpr int kIirThreads = kIirPanels * 8 * (kIirChunk / kIirJ);
 constexpr int kIirH = Prec<float>::halo;
 constexpr int kIirRows = kIirChunk + 2 * kIirH + 6;  // bound on the staged rows
-constexpr int kIirQ = 8;  // integrand stride in a staged row (4 integrands x 4 panels of a warp: distinct banks)
+constexpr int kIirQ = 8;  // integrand stride in a staged row ([4 integrands][8 panels])
 constexpr int kIirRow = 4 * kIirQ;                   // staged row stride (floats)
 
 // ---------------------------------------------------------------------------
@@ -484,7 +485,6 @@ __global__ void __launch_bounds__(kIirThreads, 6) k_prep_iir(PrepArgs<float> a) 
   float *sb = reinterpret_cast<float *>(smem_raw);
   float *sb2 = sb + kIirRows * kIirRow;
   const int tid = threadIdx.x;
-  // 1D grid over the record-end chunks (fastest), then panel tiles
   // 1D grid over the chunks of [c_lo, c_hi) outside [int_lo, int_hi) (fastest),
   // then panel tiles
   const int na = a.int_lo - a.c_lo, n_edge = na + a.c_hi - a.int_hi;
