@@ -109,6 +109,98 @@ __global__ void __launch_bounds__(256) k_adjoint(const T *coef, const T *Gt, T *
     for (int s = 0; s < kRec; ++s) out[(size_t)j * 32 * kRec + s] = acc[j][s];
 }
 
+// Set form (FP32).  Work item = (panel set, observer group, 128-sample
+// chunk), numbered observer group fastest, then chunk, then the sets in
+// descending size.  The gradient bins every (panel, observer) of the set can
+// touch in the chunk, G[k0 - i0max(o) - 1 + t] for t < win + 1 (the planner
+// bounds each record's offset i0max - i0 by the window slack), are staged in
+// shared memory once per item; each warp then takes panels of the set in
+// turn and, for every observer of the group, reads the two bins of each of
+// its samples from that window (conflict-free, consecutive lanes at
+// consecutive slots) and accumulates the 16 components of Xbar in registers.
+// One observer group writes Xbar directly; several add their partial sums
+// with vector atomics into a zeroed Xbar.
+constexpr int kAdjGroup = 36;    // observers per item
+constexpr int kAdjWarps = 4;
+constexpr int kAdjTK = 4;        // samples per lane (chunk 128)
+
+__device__ __forceinline__ void red_add_v4(float *addr, float4 v) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(addr), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w)
+               : "memory");
+}
+
+template <bool kAtomic>
+__global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint_set(AdjArgs<float> a) {
+  constexpr int CH = 32 * kAdjTK;
+  extern __shared__ __align__(16) float gw[];  // [kAdjGroup][wstride]
+  const int wstride = (a.win + 1 + 3) & ~3;
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int ng = (a.O + kAdjGroup - 1) / kAdjGroup;
+  const int nch = a.ntp / CH;
+  const int item = blockIdx.x;
+  const int g = item % ng;
+  const int rest = item / ng;
+  const int ch = rest % nch;
+  const int sidx = a.set_order[rest / nch];
+  const int k0 = ch * CH;
+  const int o0 = g * kAdjGroup;
+  const int no = min(kAdjGroup, a.O - o0);
+  const int p_begin = a.set_begin[sidx], p_end = a.set_begin[sidx + 1];
+  // stage the window of each observer of the group
+  for (int o = 0; o < no; ++o) {
+    const int base = k0 - a.i0max_tab[(size_t)sidx * a.O + o0 + o] - 1;
+    const float *G = a.Gt + (size_t)(o0 + o) * a.ntp;
+    for (int t = threadIdx.x; t <= a.win; t += blockDim.x) {
+      const int j = base + t;
+      gw[o * wstride + t] = (j >= 0 && j < a.ntp) ? G[j] : 0.f;
+    }
+  }
+  __syncthreads();
+  for (int p = p_begin + w; p < p_end; p += kAdjWarps) {
+    float acc[kAdjTK][kRec];
+#pragma unroll
+    for (int j = 0; j < kAdjTK; ++j)
+#pragma unroll
+      for (int s = 0; s < kRec; ++s) acc[j][s] = 0.f;
+    const float4 *rec = reinterpret_cast<const float4 *>(a.coef + ((size_t)p * a.O + o0) * kRec);
+    for (int o = 0; o < no; ++o) {
+      const float4 r0 = __ldg(rec + 4 * o), r1 = __ldg(rec + 4 * o + 1),
+                   r2 = __ldg(rec + 4 * o + 2), r3 = __ldg(rec + 4 * o + 3);
+      const float c[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+      const float wa = r2.x, wb = r2.y, wcc = r2.z, wdd = r2.w;  // slots a, b, cc, dd
+      const int off = __float_as_int(r3.y);                       // slot off = i0max - i0
+      // G[k - i0] at window slot (k - k0) + off + 1, G[k - i0 - 1] one below
+      const float *gp = gw + o * wstride + off + lane;
+#pragma unroll
+      for (int j = 0; j < kAdjTK; ++j) {
+        const float g1 = gp[32 * j], g0 = gp[32 * j + 1];
+        const float gF = wa * g0 + wb * g1;
+        const float gM = wcc * g0 + wdd * g1;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          acc[j][s] = fmaf(c[s], gF, acc[j][s]);
+          acc[j][8 + s] = fmaf(c[s], gM, acc[j][8 + s]);
+        }
+      }
+    }
+    float *out = a.Xbar + ((size_t)p * a.ntp + k0 + lane) * kRec;
+#pragma unroll
+    for (int j = 0; j < kAdjTK; ++j)
+#pragma unroll
+      for (int q = 0; q < kRec / 4; ++q) {
+        const float4 v = make_float4(acc[j][4 * q], acc[j][4 * q + 1], acc[j][4 * q + 2],
+                                     acc[j][4 * q + 3]);
+        float *dst = out + (size_t)j * 32 * kRec + 4 * q;
+        if (kAtomic)
+          red_add_v4(dst, v);
+        else
+          *reinterpret_cast<float4 *>(dst) = v;
+      }
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -120,6 +212,33 @@ cudaError_t launch_adjoint(const AdjArgs<T> &a, cudaStream_t s) {
   k_grad_pad<T><<<gg, 256, 0, s>>>(a.grad_p, a.n_valid, Gt, a.O, a.nt, a.ntp);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if constexpr (sizeof(T) == 4) {
+    if (a.win > 0) {
+      constexpr int SCH = 32 * kAdjTK;
+      if (a.ntp % SCH != 0) return cudaErrorInvalidValue;
+      const int ng = (a.O + kAdjGroup - 1) / kAdjGroup;
+      const long items = (long)a.nsets * ng * (a.ntp / SCH);
+      if (items <= 0) return cudaSuccess;
+      if (items > INT32_MAX) return cudaErrorInvalidValue;
+      const size_t smem = (size_t)kAdjGroup * ((a.win + 1 + 3) & ~3) * sizeof(float);
+      if (ng > 1) {
+        e = cudaMemsetAsync(a.Xbar, 0, (size_t)a.P * a.ntp * kRec * sizeof(float), s);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_adjoint_set<true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+          return e;
+        k_adjoint_set<true><<<(unsigned)items, kAdjWarps * 32, smem, s>>>(a);
+      } else {
+        if ((e = cudaFuncSetAttribute(k_adjoint_set<false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+          return e;
+        k_adjoint_set<false><<<(unsigned)items, kAdjWarps * 32, smem, s>>>(a);
+      }
+      return cudaGetLastError();
+    }
+  }
   const long blocks = (long)a.P * ((a.ntp / CH + 7) / 8);
   if (blocks <= 0) return cudaSuccess;
   k_adjoint<T, TK><<<(unsigned)blocks, 256, 0, s>>>(a.coef, Gt, a.Xbar, a.P, a.O, a.ntp);

@@ -764,6 +764,18 @@ fwh_status fwh_backward(fwh_handle h, const void *fields, int64_t nt, const doub
                       reinterpret_cast<float *>(h->G.p), dg,
                       reinterpret_cast<const int *>(h->nvalid.p),
                       reinterpret_cast<float *>(h->X.p), (int)h->P, (int)h->O, h->ntp, (int)nt};
+    // the set form gathers with the forward's plan (panel sets and each
+    // record's window offset) of a 128-sample-chunk tile shape
+    const FwdConfig c = fwd_config(false, effective_cfg(h, h->ntp));
+    if (32 * c.tk == 128) {
+      st = plan(h, c, s);
+      if (st != FWH_OK) return st;
+      aa.set_begin = reinterpret_cast<const int *>(h->sets.p);
+      aa.set_order = reinterpret_cast<const int *>(h->sord.p);
+      aa.i0max_tab = reinterpret_cast<const int *>(h->imax.p);
+      aa.nsets = (int)h->set_begin.size() - 1;
+      aa.win = c.win;
+    }
     CK(h, launch_adjoint<float>(aa, s));
     PrepAdjArgs<float> pa{reinterpret_cast<const float *>(df),
                           h->identity ? nullptr : h->d_perm, h->d_n,

@@ -100,6 +100,11 @@ struct AdjArgs {
   const int *n_valid;   // [O]
   T *Xbar;              // [P][ntp][16] gradient w.r.t. X
   int P, O, ntp, nt;
+  // FP32 set form (win > 0): the forward plan of a 128-sample-chunk shape
+  const int *set_begin; // [nsets + 1] panel-set boundaries (sorted order)
+  const int *set_order; // [nsets] sets by descending panel count
+  const int *i0max_tab; // [nsets][O] largest shift of each (panel set, observer)
+  int nsets, win;       // win: window slots per observer (chunk + slack + 1)
 };
 
 template <typename T>

@@ -208,11 +208,15 @@ def test_host_slab_pipeline_matches_device(dev, cfg):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_backward_matches_oracle_adjoint(dev, prec):
+@pytest.mark.parametrize("n_obs", [6, 80])
+def test_backward_matches_oracle_adjoint(dev, prec, n_obs):
+    """Adjoint vs the oracle's FP64 adjoint.  In the mixed form, 80 observers
+    make three 36-observer groups whose partial gradients are added with
+    atomics (6 observers: one group, direct stores)."""
     rng = np.random.default_rng(5)
     surf = uv_sphere(1.0, 9, 13)
     mach, aoa, dt, nt = 0.45, 8 * DEG, 0.04, 333
-    obs = observers_circle(20.0, 6) + rng.normal(size=(6, 3))
+    obs = observers_circle(20.0, n_obs) + rng.normal(size=(n_obs, 3))
     f = surface_fields("dipole", surf.centroids, FlowCase(mach, aoa), 0.01, 2 * np.pi, dt, nt)
     f += rng.normal(size=f.shape) * 1e-3
     s = _fwh(surf, mach, aoa, dt, prec, obs)
