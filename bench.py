@@ -64,10 +64,34 @@ def parse_args():
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: workload 2 with --nt steps, two forward calls")
     ap.add_argument("--nt", type=int, default=512)
+    ap.add_argument("--profile-backward", action="store_true",
+                    help="small case for ncu: the 16384-panel x 1024-step x 36-observer dipole, "
+                         "two forward + backward calls")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--tile-config", type=int, default=-1,
                     help="forward tile configuration index (-1: the library default)")
     return ap.parse_args()
+
+
+def profile_backward(args):
+    """Two fwh_forward + fwh_backward calls on the 16384 x 1024 x 36 dipole
+    (about 2.5 GB on the device): the capture target for the adjoint kernels."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    from paper_2312_16263_gb300 import FWH
+    from fwh_inputs import workload
+    w = workload(4)
+    s = FWH.from_workload(w, args.precision)
+    f = w.fields(device="cuda:0", dtype="float32" if args.precision == "mixed" else "float64")
+    p = s.forward(f)
+    g = 2.0 * p
+    for _ in range(2):
+        gf = s.backward(f, g)
+    torch.cuda.synchronize()
+    s.check()
+    print(json.dumps({"profile_backward": w.name, "precision": args.precision,
+                      "max_abs_grad": float(gf.abs().max())}))
 
 
 def profile_case(args):
@@ -277,6 +301,9 @@ def run_reference(args, ws, rank):
 
 def main():
     args = parse_args()
+    if args.profile_backward:
+        profile_backward(args)
+        return
     if args.profile_case:
         profile_case(args)
         return

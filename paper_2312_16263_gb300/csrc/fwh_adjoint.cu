@@ -165,9 +165,16 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint_set(AdjArgs<float> a
 #pragma unroll
       for (int s = 0; s < kRec; ++s) acc[j][s] = 0.f;
     const float4 *rec = reinterpret_cast<const float4 *>(a.coef + ((size_t)p * a.O + o0) * kRec);
+    // the next observer's record is loaded while this one is accumulated
+    float4 n0 = __ldg(rec), n1 = __ldg(rec + 1), n2 = __ldg(rec + 2), n3 = __ldg(rec + 3);
     for (int o = 0; o < no; ++o) {
-      const float4 r0 = __ldg(rec + 4 * o), r1 = __ldg(rec + 4 * o + 1),
-                   r2 = __ldg(rec + 4 * o + 2), r3 = __ldg(rec + 4 * o + 3);
+      const float4 r0 = n0, r1 = n1, r2 = n2, r3 = n3;
+      if (o + 1 < no) {
+        n0 = __ldg(rec + 4 * o + 4);
+        n1 = __ldg(rec + 4 * o + 5);
+        n2 = __ldg(rec + 4 * o + 6);
+        n3 = __ldg(rec + 4 * o + 7);
+      }
       const float c[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
       const float wa = r2.x, wb = r2.y, wcc = r2.z, wdd = r2.w;  // slots a, b, cc, dd
       const int off = __float_as_int(r3.y);                       // slot off = i0max - i0
