@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 CPU oracle, element by element (needs a GPU).
 
-Tolerances (spec contract): rel-L2 per observer signal <= 1e-10 for the
+Tolerances (the accuracy bar of the two forms): rel-L2 per observer signal <= 1e-10 for the
 FP64 path and <= 1e-4 for the mixed path, compared on the common prefix of
 the two observer windows (N_o comes from a floor() of FP64 values that may
 round differently).  Cases span several tiles with ragged tails: panel
