@@ -41,7 +41,7 @@ FP64_PEAK_TFLOPS = 1.25
 
 
 def hbm_peak_gbs():
-    """Measured copy bandwidth of this GPU pool (GB/s), else the earlier
+    """HBM copy bandwidth measured on these GB300s (GB/s), else an earlier
     GB300 measurement."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
