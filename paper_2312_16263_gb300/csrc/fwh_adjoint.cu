@@ -6,10 +6,14 @@
 // loss with respect to p_out (zero outside the valid bins 0 <= j < N_o), is
 //   gF = a G[k - i0] + b G[k - i0 - 1],   gM = cc G[k - i0] + dd G[k - i0 - 1]
 //   Xbar[p][k][s]     = sum_o c_s gF,     Xbar[p][k][8 + s] = sum_o c_s gM,
-// so each (panel, sample) output is owned by one lane and summed over all
-// observers in registers: no atomics, 20 FMA per (panel, sample, observer).
+// so each (panel, sample) output is owned by one lane and summed over the
+// observers in registers, 20 FMA per (panel, sample, observer).  Two forms:
+// k_adjoint_set (FP32) gathers per panel set from a window of G staged in
+// shared memory, with atomics only to add the partial sums of several
+// 36-observer groups; k_adjoint (FP64, and FP32 shapes with 256-sample
+// chunks) is one CTA per panel reading G from L2, without atomics.
 // Nothing from the forward pass is stored: only the per-(p, o) records
-// (geometry, computed once per observer set) and G are read.
+// (geometry, computed once per observer set), the plan and G are read.
 #include "fwh_internal.cuh"
 
 namespace fwh {
