@@ -213,6 +213,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measured_fma_peaks():
+    """FP32 and FP64 FMA throughput of this GPU (TFLOP/s) from the library's
+    FMA-chain probe (fwh_fma_peak), taken before the timed region."""
+    import ctypes
+    from paper_2312_16263_gb300 import _abi
+    lib = _abi.load()
+    out = {}
+    for name, prec in (("fp32", _abi.FWH_MIXED), ("fp64", _abi.FWH_FP64)):
+        v = ctypes.c_double(0.0)
+        _abi.check(lib.fwh_fma_peak(prec, ctypes.byref(v), None))
+        out[name] = v.value
+    return out
+
+
 def profile_traffic():
     """DRAM bytes per forward launch from the committed ncu summary, if that
     summary was taken on the current kernel source (hash match), else None."""
@@ -320,6 +334,7 @@ def main():
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    peaks = measured_fma_peaks()
     w = rank_workload(rank, ws)
     evals = w.evals
     s = FWH.from_workload(w, "mixed")
@@ -415,13 +430,18 @@ def main():
                      "traffic": traffic,
                      "kernel": "k_forward (forward scatter)",
                      "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "peak_measured": peaks["fp32"],
+                     "frac_of_measured": achieved / peaks["fp32"],
+                     "peak_measured_source": "FMA-chain probe fwh_fma_peak (FP32)",
                      "kernel_ms": fwd_ms, "prep_ms": prep_ms,
                      "flop_per_eval": FLOP_PER_EVAL},
         "fp64": {"value": evals * ws / (max_over_ranks(ms64, ws) / 1e3), "unit": UNIT,
                  "ms_per_step": ms64, "kernel_ms": fwd64,
                  "achieved_tflops": evals * FLOP_PER_EVAL / (fwd64 / 1e3) / 1e12,
                  "peak_tflops": FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64",
-                 "frac": evals * FLOP_PER_EVAL / (fwd64 / 1e3) / 1e12 / FP64_PEAK_TFLOPS},
+                 "frac": evals * FLOP_PER_EVAL / (fwd64 / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                 "peak_measured": peaks["fp64"],
+                 "frac_of_measured": evals * FLOP_PER_EVAL / (fwd64 / 1e3) / 1e12 / peaks["fp64"]},
         "accuracy": {"mixed_vs_fp64_rel_l2_max": float(rel_mixed_fp64.max()),
                      "mixed_vs_fp64_rel_l2_median": float(np.median(rel_mixed_fp64))},
         "e2e": {"value": evals * ws / (e2e_ms_max / 1e3), "unit": UNIT,

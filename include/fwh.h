@@ -35,6 +35,14 @@
  *    Device work is enqueued on it; calls with host outputs synchronise it.
  *  - Every call returns a status and never aborts; fwh_last_error() gives a
  *    message for the last failing call on that handle.
+ *  - Device-side checks (a bounded wait that gave up, a panel set whose
+ *    arrival spread exceeded its window) raise a flag on the device.  Calls
+ *    with host outputs read it before returning.  Calls whose outputs stay on
+ *    the device copy it to pinned host memory behind their work, and the next
+ *    call on the handle (forward, backward, batched or allocation-free
+ *    forward) that finds that copy complete reports it as its own status
+ *    (FWH_ERR_TIMEOUT or FWH_ERR_CUDA, message "an earlier call on this
+ *    handle: ...") without running; fwh_check reports it synchronously.
  */
 #ifndef FWH_H_
 #define FWH_H_
@@ -99,10 +107,11 @@ fwh_status fwh_set_observers(fwh_handle h, int64_t n_obs, const double *xyz);
  * 256 frames or more are copied in 128-frame slabs on streams the handle owns,
  * overlapped with the preparation and scatter of the frames already copied;
  * the call still returns only when p_out holds the result.
- * Errors: FWH_ERR_STATE before fwh_set_observers, FWH_ERR_ARG for nt < 3,
- * null pointers, or (FWH_MIXED) n_panels x round_up(nt, 256) >= 2^32 (series
- * rows are addressed with 32-bit indices; checked before any work, the handle
- * stays usable), FWH_ERR_CUDA / FWH_ERR_OOM on device failure.
+ * Errors: FWH_ERR_STATE before fwh_set_observers, FWH_ERR_ARG for nt outside
+ * [3, 2^28], null pointers, or (FWH_MIXED) n_panels x round_up(nt, 256) >= 2^32
+ * (series rows are addressed with 32-bit indices; checked before any work, the
+ * handle stays usable), FWH_ERR_CUDA / FWH_ERR_OOM on device failure, or the
+ * deferred device check of an earlier call (see the conventions above).
  */
 fwh_status fwh_forward(fwh_handle h, const void *fields, int64_t nt, double *p_out,
                        void *stream);
@@ -129,7 +138,7 @@ fwh_status fwh_backward(fwh_handle h, const void *fields, int64_t nt,
 /*
  * Batched forward over n handles (several uneven surfaces, each with its own
  * observers, fields, nt and p_out), run by one persistent work-queue kernel
- * per time segment; all handles must share one precision.  With device
+ * over the work items of every surface; all handles must share one precision.  With device
  * buffers the launch sequence is captured once in a CUDA graph keyed on the
  * handle set and replayed on later calls with the same arguments.
  * Errors: FWH_ERR_ARG (n < 1, mixed precisions, null entries),
@@ -171,19 +180,37 @@ fwh_status fwh_timing_totals(fwh_handle h, double *ms3, int64_t *calls, int rese
  * Synchronise `stream` and report the device-side checks raised by this
  * handle's kernels since the last check (a panel set whose arrival spread
  * exceeded its window -> FWH_ERR_CUDA; a bounded wait that gave up ->
- * FWH_ERR_TIMEOUT).  Calls with host outputs run this check themselves.
+ * FWH_ERR_TIMEOUT), then clear them.  Calls with host outputs run this check
+ * themselves.
  */
 fwh_status fwh_check(fwh_handle h, void *stream);
+
+/*
+ * Bound, in SM clock cycles, of each wait of the forward kernel's copy
+ * pipeline (a compute warp waiting for its stage, the copy warp waiting for a
+ * free one); 0 restores the default of 4e9 cycles (about 2 s).  A wait that
+ * runs out raises FWH_ERR_TIMEOUT through the device check, the kernel stops
+ * issuing copies, waits (always with the default bound) for those in flight
+ * and returns; p_out of that call is then incomplete, and the handle stays
+ * usable.  Meant for testing that error path: a bound of a few cycles runs
+ * out on any forward call.  Errors: FWH_ERR_ARG for a negative bound.
+ */
+fwh_status fwh_set_wait_limit(fwh_handle h, int64_t cycles);
 
 /*
  * Forward pass that allocates no device memory.  The paper has no
  * counterpart: this exists for callers that cannot call cudaMalloc/cudaFree
  * or any allocator while they run (a real-time loop with a memory budget
- * fixed up front, a host callback, code embedded in a framework that owns
- * the device memory and forbids allocation during a step).  Results equal
- * fwh_forward's.  The handle must have been set up earlier (fwh_create and
- * fwh_set_observers allocate); fields and p_out must be device pointers
- * (FWH_ERR_ARG otherwise: there is no staging).
+ * fixed up front, code embedded in a framework that owns the device memory
+ * and forbids allocation during a step).  Results equal fwh_forward's.  The
+ * handle must have been set up earlier (fwh_create and fwh_set_observers
+ * allocate); fields and p_out must be device pointers (FWH_ERR_ARG
+ * otherwise: there is no staging).  The call copies nothing from host memory
+ * (observer windows are computed on the device, the series descriptor is a
+ * kernel parameter) and writes no buffer of the handle besides its device
+ * error flag: it reads the handle's panel-set plan, which fwh_set_observers,
+ * fwh_set_tile_config and fwh_autotune leave in place for the configured tile
+ * shape (FWH_ERR_STATE if a forward call on a huge record replaced it).
  * Scratch: the prepared series and per-call tables live in one file-scope
  * device array of 64 MiB that every GPU loading the library reserves until
  * the process exits; a problem needing more (about P x round_up(nt, 256) x
@@ -196,6 +223,17 @@ fwh_status fwh_check(fwh_handle h, void *stream);
  */
 fwh_status fwh_forward_noalloc(fwh_handle h, const void *fields, int64_t nt, double *p_out,
                                void *stream);
+
+/*
+ * Measured fused multiply-add throughput of the current GPU (TFLOP/s, 2 flop
+ * per FMA): FP32 for FWH_MIXED, FP64 for FWH_FP64, from independent FMA
+ * chains on every SM timed with CUDA events on `stream` (about 60 ms; the
+ * call synchronises).  The forward scatter is bound by this rate, not by
+ * memory or a dense contraction, so this is its measured roof.  Not part of
+ * the paper's method.  Errors: FWH_ERR_ARG, FWH_ERR_CUDA (message via
+ * fwh_last_error(NULL)).
+ */
+fwh_status fwh_fma_peak(int precision, double *tflops, void *stream);
 
 /* Number of panels, observers and the precision of a handle. */
 fwh_status fwh_get_sizes(fwh_handle h, int64_t *n_panels, int64_t *n_obs,

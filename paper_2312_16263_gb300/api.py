@@ -92,7 +92,10 @@ class FWH:
             raise ValueError("fields must be contiguous")
 
     def forward(self, fields: torch.Tensor, out: torch.Tensor | None = None, stream=None):
-        """p_out [O][nt] float64 on the fields' device (host fields -> host output)."""
+        """p_out [O][nt] float64 on the fields' device (host fields -> host output).
+
+        A device-side check that fails during a call with device outputs is
+        raised (FWHError) by the next call on this surface, or by check()."""
         self._check_fields(fields)
         nt = fields.shape[0]
         if out is None:
@@ -124,6 +127,10 @@ class FWH:
 
     def set_tile_config(self, idx: int):
         _abi.check(self.lib.fwh_set_tile_config(self.h, int(idx)), self.h)
+
+    def set_wait_limit(self, cycles: int = 0):
+        """Bound (SM clocks) of the forward pipeline's waits; 0 = default."""
+        _abi.check(self.lib.fwh_set_wait_limit(self.h, int(cycles)), self.h)
 
     def set_timing(self, enable: bool = True):
         _abi.check(self.lib.fwh_set_timing(self.h, int(bool(enable))), self.h)

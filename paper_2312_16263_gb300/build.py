@@ -21,7 +21,10 @@ LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(LIBDIR, "libfwh_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code: no fused multiply-add contraction, so the planner rounds alike on
+# x86-64 and Arm (and exactly as the device's observer-window kernel)
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+         "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
 
 

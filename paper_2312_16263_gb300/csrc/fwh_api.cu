@@ -62,9 +62,19 @@ struct fwh_ctx {
   double *d_Rmax = nullptr, *d_Rmin = nullptr;
   int *d_perm = nullptr, *d_err = nullptr;
   Buf coef, X, G, nvalid, sets, sord, stage_in, stage_out, stage_grad, tmap, imax;
-  const void *tmap_X = nullptr;  // X buffer / rows / box the device descriptor describes
+  // X tensor map: host copy (passed to single launches as a kernel parameter)
+  // and, for the batched form, a device copy
+  alignas(64) unsigned char tmap_host[128] = {};
+  const void *tmap_X = nullptr;  // X buffer / rows / box the host descriptor describes
   int tmap_box = 0;
   long long tmap_rows = 0;
+  bool tmap_dev_ok = false;      // the device copy equals the host descriptor
+  long long wait_limit = 0;      // bound of the forward pipeline waits (0: default)
+  // deferred device check: each call with device outputs copies the error flag
+  // into pinned host memory; the next call (or fwh_check) reads it
+  int *h_err = nullptr;
+  cudaEvent_t err_ev = nullptr;
+  bool err_pending = false;
   // per-nt
   int64_t nt = -1;
   int ntp = 0;
@@ -243,7 +253,11 @@ fwh_status plan(fwh_handle h, const FwdConfig &c, cudaStream_t s) {
 
 // Per-nt window and workspace.  ntp is a multiple of 256, hence of every
 // forward chunk (32 x TK samples) and prep chunk.
+constexpr int64_t kMaxNt = (int64_t)1 << 28;
+
 fwh_status prepare_nt(fwh_handle h, int64_t nt) {
+  if (nt < 3 || nt > kMaxNt)
+    return fail(h, FWH_ERR_ARG, "nt must be in [3, 2^28] (got " + std::to_string(nt) + ")");
   if (h->precision == FWH_MIXED && h->P * ((nt + 255) / 256 * 256) >= ((int64_t)1 << 32))
     return fail(h, FWH_ERR_ARG, "panels x padded steps must stay below 2^32 per handle");
   if (h->nt != nt) {
@@ -283,21 +297,40 @@ int effective_cfg(const fwh_ctx *h, int64_t ntp) {
   return cfg;
 }
 
-// Device-resident TMA descriptor of the handle's X buffer (re-encoded when
+// Panel-set plan of the handle's configured tile shape, made at set-up
+// (fwh_set_observers, fwh_set_tile_config, fwh_autotune), so that calls which
+// must not allocate or copy from the host find it in place.
+fwh_status plan_default(fwh_handle h) {
+  const FwdConfig c = fwd_config(h->precision == FWH_FP64, h->cfg >= 0 ? h->cfg : default_cfg(h));
+  fwh_status st = plan(h, c, 0);
+  if (st != FWH_OK) return st;
+  CK(h, cudaStreamSynchronize(0));
+  return FWH_OK;
+}
+
+// TMA descriptor of the handle's X buffer, kept on the host (re-encoded when
 // the buffer, its row count or the box changes).
 fwh_status ensure_tmap(fwh_handle h, int box_rows) {
   const long long rows = (long long)h->P * h->ntp;
-  if (h->tmap.p && h->tmap_X == h->X.p && h->tmap_rows == rows && h->tmap_box == box_rows)
-    return FWH_OK;
-  alignas(64) unsigned char desc[128];
-  if (!encode_x_tensor_map(desc, h->X.p, (unsigned long long)rows,
+  if (h->tmap_X == h->X.p && h->tmap_rows == rows && h->tmap_box == box_rows) return FWH_OK;
+  if (!encode_x_tensor_map(h->tmap_host, h->X.p, (unsigned long long)rows,
                            h->precision == FWH_FP64, box_rows))
     return fail(h, FWH_ERR_CUDA, "cuTensorMapEncodeTiled refused the series layout");
-  CK(h, ensure(h->tmap, 128));
-  CK(h, cudaMemcpy(h->tmap.p, desc, 128, cudaMemcpyHostToDevice));
   h->tmap_X = h->X.p;
   h->tmap_rows = rows;
   h->tmap_box = box_rows;
+  h->tmap_dev_ok = false;
+  return FWH_OK;
+}
+
+// Device copy of the descriptor, for the batched form's argument table.
+fwh_status ensure_tmap_dev(fwh_handle h, int box_rows) {
+  fwh_status st = ensure_tmap(h, box_rows);
+  if (st != FWH_OK) return st;
+  if (h->tmap.p && h->tmap_dev_ok) return FWH_OK;
+  CK(h, ensure(h->tmap, 128));
+  CK(h, cudaMemcpy(h->tmap.p, h->tmap_host, 128, cudaMemcpyHostToDevice));
+  h->tmap_dev_ok = true;
   return FWH_OK;
 }
 
@@ -346,7 +379,8 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
   pa.sa = h->sa;
   pa.dt = h->dt;
   FwdArgs<T> fa{};
-  fa.tmX = h->tmap.p;
+  fa.tmX = nullptr;
+  fa.wait_cycles = h->wait_limit;
   fa.X = pa.X;
   fa.coef = reinterpret_cast<const T *>(h->coef.p);
   fa.p_out = d_pout;
@@ -368,7 +402,7 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
   if (host_fields == nullptr) {
     CK(h, launch_prep<T>(pa, s));
     if (tev) CK(h, cudaEventRecord(tev[1], s));
-    CK(h, launch_forward<T>(fa, cfg, s));
+    CK(h, launch_forward<T>(fa, c.pipe ? h->tmap_host : nullptr, cfg, s));
   } else {
     // Three streams: `copy` moves the slabs, `prep` (high priority, so that
     // its blocks get onto SMs between the scatter's) prepares slab q - 1 once
@@ -406,7 +440,7 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
       if (tev && seg_done == 0) CK(h, cudaEventRecord(tev[1], s));
       fa.seg_lo = seg_done;
       fa.seg_cnt = ready - seg_done;
-      CK(h, launch_forward<T>(fa, cfg, s));
+      CK(h, launch_forward<T>(fa, c.pipe ? h->tmap_host : nullptr, cfg, s));
       seg_done = ready;
       return FWH_OK;
     };
@@ -466,16 +500,57 @@ fwh_status drain_timings(fwh_handle h) {
   return FWH_OK;
 }
 
+// Status and message of a nonzero device flag.
+fwh_status flag_failure(fwh_handle h, int flag, const char *when) {
+  std::string m = when;
+  if (flag & kErrTimeout) m += ": a bounded device-side wait gave up";
+  if (flag & kErrWindow) m += ": a panel set's arrival spread exceeded its window";
+  if (flag & kErrQueue) m += ": the persistent work queue was inconsistent";
+  return fail(h, (flag & kErrTimeout) ? FWH_ERR_TIMEOUT : FWH_ERR_CUDA,
+              m + " (device flags " + std::to_string(flag) + ")");
+}
+
+// Synchronous check: wait for `s` and read (and clear) the device flag.
 fwh_status check_device_flag(fwh_handle h, cudaStream_t s) {
   int flag = 0;
   CK(h, cudaMemcpyAsync(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
+  h->err_pending = false;
   if (flag) {
     CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
-    if (flag & kErrTimeout) return fail(h, FWH_ERR_TIMEOUT, "device wait timed out");
-    return fail(h, FWH_ERR_CUDA, "device check failed (flags " + std::to_string(flag) + ")");
+    CK(h, cudaStreamSynchronize(s));
+    return flag_failure(h, flag, "device check");
   }
   return FWH_OK;
+}
+
+// After a call whose outputs stay on the device: copy the flag into pinned
+// host memory behind the call's work, so that a later call can report it
+// without waiting.
+fwh_status defer_check(fwh_handle h, cudaStream_t s) {
+  CK(h, cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaEventRecord(h->err_ev, s));
+  h->err_pending = true;
+  return FWH_OK;
+}
+
+// At the start of a call: report a failure of an earlier call whose flag copy
+// has completed (never waits; a copy still in flight is looked at later).
+fwh_status take_deferred(fwh_handle h) {
+  if (!h->err_pending) return FWH_OK;
+  const cudaError_t q = cudaEventQuery(h->err_ev);
+  if (q == cudaErrorNotReady) {
+    cudaGetLastError();
+    return FWH_OK;
+  }
+  if (q != cudaSuccess) return cuda_fail(h, q, "cudaEventQuery");
+  h->err_pending = false;
+  const int flag = *h->h_err;
+  if (!flag) return FWH_OK;
+  *h->h_err = 0;
+  CK(h, cudaMemset(h->d_err, 0, sizeof(int)));
+  CK(h, cudaDeviceSynchronize());
+  return flag_failure(h, flag, "an earlier call on this handle");
 }
 
 }  // namespace
@@ -604,6 +679,12 @@ fwh_status fwh_create(fwh_handle *out, int64_t P, const double *centroids,
       fwh_destroy(h);
       return cuda_fail(nullptr, e, "cudaEventCreate");
     }
+  if ((e = cudaHostAlloc(&h->h_err, sizeof(int), cudaHostAllocDefault)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&h->err_ev, cudaEventDisableTiming)) != cudaSuccess) {
+    fwh_destroy(h);
+    return cuda_fail(nullptr, e, "fwh_create error-flag setup");
+  }
+  *h->h_err = 0;
   *out = h;
   return FWH_OK;
 }
@@ -659,13 +740,12 @@ fwh_status fwh_set_observers(fwh_handle h, int64_t O, const double *xyz) {
   h->nt = -1;         // window depends on the observers
   h->plan_win = -1;   // records were rewritten: window offsets must be re-planned
   drop_graphs(h);
-  return FWH_OK;
+  return plan_default(h);
 }
 
 fwh_status fwh_observer_window(fwh_handle h, int64_t nt, double *t_start, int64_t *n_valid) {
   if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
   if (h->O < 1) return fail(h, FWH_ERR_STATE, "observers not set");
-  if (nt < 3 || nt > (int64_t)1 << 28) return fail(h, FWH_ERR_ARG, "nt must be >= 3");
   fwh_status st = prepare_nt(h, nt);
   if (st != FWH_OK) return st;
   for (int64_t o = 0; o < h->O; ++o) {
@@ -680,9 +760,10 @@ fwh_status fwh_forward(fwh_handle h, const void *fields, int64_t nt, double *p_o
   if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
   if (h->O < 1) return fail(h, FWH_ERR_STATE, "fwh_set_observers must come first");
   if (!fields || !p_out) return fail(h, FWH_ERR_ARG, "fields or p_out is NULL");
-  if (nt < 3 || nt > (int64_t)1 << 28) return fail(h, FWH_ERR_ARG, "nt must be >= 3");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  fwh_status st = prepare_nt(h, nt);
+  fwh_status st = take_deferred(h);
+  if (st != FWH_OK) return st;
+  st = prepare_nt(h, nt);
   if (st != FWH_OK) return st;
   const size_t ts = tsize(h->precision);
   const size_t fbytes = (size_t)nt * 5 * h->P * ts;
@@ -711,7 +792,7 @@ fwh_status fwh_forward(fwh_handle h, const void *fields, int64_t nt, double *p_o
     CK(h, cudaMemcpyAsync(p_out, dp, obytes, cudaMemcpyDeviceToHost, s));
     return check_device_flag(h, s);
   }
-  return FWH_OK;
+  return defer_check(h, s);
 }
 
 fwh_status fwh_backward(fwh_handle h, const void *fields, int64_t nt, const double *grad_p,
@@ -720,9 +801,10 @@ fwh_status fwh_backward(fwh_handle h, const void *fields, int64_t nt, const doub
   if (h->O < 1) return fail(h, FWH_ERR_STATE, "fwh_set_observers must come first");
   if (!fields || !grad_p || !grad_fields)
     return fail(h, FWH_ERR_ARG, "fields, grad_p or grad_fields is NULL");
-  if (nt < 3 || nt > (int64_t)1 << 28) return fail(h, FWH_ERR_ARG, "nt must be >= 3");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  fwh_status st = prepare_nt(h, nt);
+  fwh_status st = take_deferred(h);
+  if (st != FWH_OK) return st;
+  st = prepare_nt(h, nt);
   if (st != FWH_OK) return st;
   const size_t ts = tsize(h->precision);
   const size_t fbytes = (size_t)nt * 5 * h->P * ts;
@@ -788,7 +870,7 @@ fwh_status fwh_backward(fwh_handle h, const void *fields, int64_t nt, const doub
     CK(h, cudaMemcpyAsync(grad_fields, dgf, fbytes, cudaMemcpyDeviceToHost, s));
     return check_device_flag(h, s);
   }
-  return FWH_OK;
+  return defer_check(h, s);
 }
 
 fwh_status fwh_set_tile_config(fwh_handle h, int config) {
@@ -797,13 +879,12 @@ fwh_status fwh_set_tile_config(fwh_handle h, int config) {
     return fail(h, FWH_ERR_ARG, "tile config out of range");
   h->cfg = config;
   drop_graphs(h);
-  return FWH_OK;
+  return h->O >= 1 ? plan_default(h) : FWH_OK;
 }
 
 fwh_status fwh_autotune(fwh_handle h, int64_t nt, int *chosen, void *stream) {
   if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
   if (h->O < 1) return fail(h, FWH_ERR_STATE, "fwh_set_observers must come first");
-  if (nt < 3) return fail(h, FWH_ERR_ARG, "nt must be >= 3");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   fwh_status st = prepare_nt(h, nt);
   if (st != FWH_OK) return st;
@@ -847,6 +928,15 @@ fwh_status fwh_autotune(fwh_handle h, int64_t nt, int *chosen, void *stream) {
   h->cfg = besti;
   (void)old;
   if (chosen) *chosen = besti;
+  drop_graphs(h);
+  return plan_default(h);
+}
+
+fwh_status fwh_set_wait_limit(fwh_handle h, int64_t cycles) {
+  if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
+  if (cycles < 0) return fail(h, FWH_ERR_ARG, "wait limit must be >= 0");
+  h->wait_limit = cycles;
+  drop_graphs(h);
   return FWH_OK;
 }
 
@@ -907,6 +997,8 @@ void fwh_destroy(fwh_handle h) {
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   for (int i = 0; i < 2; ++i)
     if (h->bev[i]) cudaEventDestroy(h->bev[i]);
+  if (h->err_ev) cudaEventDestroy(h->err_ev);
+  if (h->h_err) cudaFreeHost(h->h_err);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->copy) cudaStreamDestroy(h->copy);
   if (h->pstream) cudaStreamDestroy(h->pstream);
@@ -943,11 +1035,12 @@ fwh_status batch_build(int n, const fwh_handle *hs, const void *const *fields,
     if (st != FWH_OK) return fail(h0, st, h->err);
     CK(h0, cudaStreamSynchronize(h0->side));
     if (c.pipe != 0) {
-      st = ensure_tmap(h, 32 * c.tk);
+      st = ensure_tmap_dev(h, 32 * c.tk);
       if (st != FWH_OK) return fail(h0, st, h->err);
     }
     FwdArgs<T> &fa = args[i];
     fa.tmX = h->tmap.p;
+    fa.wait_cycles = h0->wait_limit;
     fa.X = reinterpret_cast<const T *>(h->X.p);
     fa.coef = reinterpret_cast<const T *>(h->coef.p);
     fa.p_out = p_out[i];
@@ -1023,12 +1116,15 @@ extern "C" fwh_status fwh_batch_forward(int n, const fwh_handle *hs, const void 
   fwh_handle h0 = hs[0];
   if (!h0) return fail(nullptr, FWH_ERR_ARG, "NULL handle in batch");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  {
+    const fwh_status st0 = take_deferred(h0);
+    if (st0 != FWH_OK) return st0;
+  }
   for (int i = 0; i < n; ++i) {
     fwh_handle h = hs[i];
     if (!h || !fields[i] || !p_out[i]) return fail(h0, FWH_ERR_ARG, "NULL entry in batch");
     if (h->precision != h0->precision) return fail(h0, FWH_ERR_ARG, "mixed precisions in batch");
     if (h->O < 1) return fail(h0, FWH_ERR_STATE, "a handle has no observers");
-    if (nt[i] < 3) return fail(h0, FWH_ERR_ARG, "nt must be >= 3");
     if (!is_device_ptr(fields[i]) || !is_device_ptr(p_out[i]))
       return fail(h0, FWH_ERR_ARG, "batched forward takes device buffers");
     fwh_status st = prepare_nt(h, nt[i]);
@@ -1048,6 +1144,7 @@ extern "C" fwh_status fwh_batch_forward(int n, const fwh_handle *hs, const void 
     key.push_back((uintptr_t)hs[i]->imax.p);
   }
   key.push_back((uintptr_t)(h0->cfg + 1));
+  key.push_back((uintptr_t)h0->wait_limit);
   if (!h0->side) {
     CK(h0, cudaStreamCreateWithFlags(&h0->side, cudaStreamNonBlocking));
     CK(h0, cudaEventCreateWithFlags(&h0->bev[0], cudaEventDisableTiming));
@@ -1083,7 +1180,7 @@ extern "C" fwh_status fwh_batch_forward(int n, const fwh_handle *hs, const void 
   CK(h0, cudaGraphLaunch(it->second.exec, h0->side));
   CK(h0, cudaEventRecord(h0->bev[1], h0->side));
   CK(h0, cudaStreamWaitEvent(s, h0->bev[1], 0));
-  return FWH_OK;
+  return defer_check(h0, s);
 }
 
 extern "C" fwh_status fwh_check(fwh_handle h, void *stream) {
@@ -1092,63 +1189,42 @@ extern "C" fwh_status fwh_check(fwh_handle h, void *stream) {
 }
 
 // ---------------------------------------------------------------------------
-// Forward pass into caller-provided device scratch (no device allocation).
-// Used by the static-scratch entry point in fwh_noalloc.cu.  Every byte of
-// the scratch that this call reads is written earlier in the same call:
-// observer windows and panel sets are copied in, every row of the prepared
-// series (including the zero rows past nt) is written by the prep kernel.
+// Forward pass into caller-provided device scratch (no device allocation, no
+// copy from host memory).  Used by the static-scratch entry point in
+// fwh_noalloc.cu.  It reads the handle's panel-set plan, which the set-up calls
+// (fwh_set_observers, fwh_set_tile_config, fwh_autotune) leave in place, and
+// changes no handle state.  Every byte of the scratch that this call reads is
+// written earlier in the same call: the observer windows by k_nvalid, every
+// row of the prepared series (including the zero rows past nt) by the prep.
 // ---------------------------------------------------------------------------
 namespace {
-
-size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
 template <typename T>
 fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, double *d_pout,
                                   cudaStream_t s, unsigned char *scratch, size_t cap) {
   const bool fp64 = sizeof(T) == 8;
-  const int ntp0 = (int)((nt + 255) / 256 * 256);
-  const int cfg = effective_cfg(h, ntp0);
+  const int ntp = (int)((nt + 255) / 256 * 256);  // same padding as prepare_nt
+  const int cfg = effective_cfg(h, ntp);
   const FwdConfig c = fwd_config(fp64, cfg);
-  // observer window (Eqs. t_start, t_end), as prepare_nt but into host temporaries
-  std::vector<int> nv(h->O);
-  const double tau_max = (double)(nt - 1) * h->dt;
-  for (int64_t o = 0; o < h->O; ++o) {
-    const double ts = h->mach * h->Rmax[o];
-    const double te = tau_max + h->mach * h->Rmin[o];
-    double v = std::floor((te - ts) / h->dt) + 1.0;
-    nv[o] = (int)std::max(0.0, std::min((double)nt, v));
-  }
-  const std::vector<int> sets = build_sets(h->y, h->P, h->mach, h->dt, c.win - 32 * c.tk - 1);
-  const int ntp = ntp0;                        // same padding as prepare_nt
-  const int nsets = (int)sets.size() - 1;
-  const size_t off_tm = round256((size_t)h->O * sizeof(int));
-  const size_t off_sets = off_tm + 256;
-  const size_t off_imax = off_sets + round256(sets.size() * sizeof(int));
-  const size_t off_x = (off_imax + round256((size_t)nsets * h->O * sizeof(int)) + 1023) / 1024 * 1024;
+  const size_t off_x = ((size_t)h->O * sizeof(int) + 1023) / 1024 * 1024;
   const size_t need = off_x + (size_t)h->P * ntp * kRec * sizeof(T);
   if (need > cap)
     return fail(h, FWH_ERR_ARG,
                 "problem needs " + std::to_string(need) + " bytes of scratch (panels x nt rounded "
                 "up to 256 x 16 values + windows); the static scratch holds " +
                     std::to_string(cap) + " bytes");
+  if (h->plan_win != c.win || h->plan_ch != 32 * c.tk)
+    return fail(h, FWH_ERR_STATE,
+                "the handle's panel-set plan belongs to another tile shape; call "
+                "fwh_set_tile_config (which plans without a forward pass) first");
   int *d_nv = reinterpret_cast<int *>(scratch);
-  int *d_sets = reinterpret_cast<int *>(scratch + off_sets);
-  int *d_imax = reinterpret_cast<int *>(scratch + off_imax);
   T *d_X = reinterpret_cast<T *>(scratch + off_x);
-  CK(h, cudaMemcpyAsync(d_nv, nv.data(), nv.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-  CK(h, cudaMemcpyAsync(d_sets, sets.data(), sets.size() * sizeof(int), cudaMemcpyHostToDevice,
-                        s));
-  if (c.pipe != 0) {
-    alignas(64) unsigned char desc[128];
-    if (!encode_x_tensor_map(desc, d_X, (unsigned long long)h->P * ntp, fp64, 32 * c.tk))
-      return fail(h, FWH_ERR_CUDA, "cuTensorMapEncodeTiled refused the series layout");
-    CK(h, cudaMemcpyAsync(scratch + off_tm, desc, 128, cudaMemcpyHostToDevice, s));
-  }
-  // window offsets of this plan (the handle's records get the same values a
-  // regular call with this configuration writes)
-  CK(h, launch_plan<T>(reinterpret_cast<T *>(h->coef.p), d_sets, nsets, (int)h->O,
-                       c.win - 32 * c.tk - 1, d_imax, h->d_err, s));
-  h->plan_win = -1;  // the handle's own set table may belong to another plan
+  // observer windows (Eqs. t_start, t_end) on the device, from R_max / R_min
+  CK(h, launch_nvalid(h->d_Rmax, h->d_Rmin, (int)h->O, h->mach, h->dt, (int)nt, d_nv, s));
+  alignas(64) unsigned char desc[128];
+  if (c.pipe != 0 &&
+      !encode_x_tensor_map(desc, d_X, (unsigned long long)h->P * ntp, fp64, 32 * c.tk))
+    return fail(h, FWH_ERR_CUDA, "cuTensorMapEncodeTiled refused the series layout");
   CK(h, cudaMemsetAsync(d_pout, 0, (size_t)h->O * nt * sizeof(double), s));
   PrepArgs<T> pa{};
   pa.fields = d_fields;
@@ -1163,15 +1239,17 @@ fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, d
   pa.dt = h->dt;
   CK(h, launch_prep<T>(pa, s));
   FwdArgs<T> fa{};
-  fa.tmX = scratch + off_tm;
+  fa.tmX = nullptr;
+  fa.wait_cycles = h->wait_limit;
   fa.X = d_X;
   fa.coef = reinterpret_cast<const T *>(h->coef.p);
   fa.p_out = d_pout;
   fa.n_valid = d_nv;
-  fa.set_begin = d_sets;
-  fa.i0max_tab = d_imax;
+  fa.set_begin = reinterpret_cast<const int *>(h->sets.p);
+  fa.set_order = reinterpret_cast<const int *>(h->sord.p);
+  fa.i0max_tab = reinterpret_cast<const int *>(h->imax.p);
   fa.err = h->d_err;
-  fa.nsets = (int)sets.size() - 1;
+  fa.nsets = (int)h->set_begin.size() - 1;
   fa.O = (int)h->O;
   fa.ntp = ntp;
   fa.nt = (int)nt;
@@ -1181,8 +1259,8 @@ fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, d
   fa.seg_lo = 0;
   fa.seg_cnt = fa.n_segs;
   fa.win = c.win;
-  CK(h, launch_forward<T>(fa, cfg, s));
-  return FWH_OK;
+  CK(h, launch_forward<T>(fa, c.pipe ? desc : nullptr, cfg, s));
+  return defer_check(h, s);
 }
 
 }  // namespace
@@ -1193,10 +1271,13 @@ fwh_status fwh_forward_into_scratch(fwh_handle h, const void *fields, int64_t nt
   if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
   if (h->O < 1) return fail(h, FWH_ERR_STATE, "fwh_set_observers must come first");
   if (!fields || !p_out) return fail(h, FWH_ERR_ARG, "fields or p_out is NULL");
-  if (nt < 3 || nt > (int64_t)1 << 28) return fail(h, FWH_ERR_ARG, "nt must be >= 3");
+  if (nt < 3 || nt > kMaxNt)
+    return fail(h, FWH_ERR_ARG, "nt must be in [3, 2^28] (got " + std::to_string(nt) + ")");
   if (!scratch) return fail(h, FWH_ERR_ARG, "scratch is NULL");
   if (!is_device_ptr(fields) || !is_device_ptr(p_out))
     return fail(h, FWH_ERR_ARG, "this entry point takes device buffers only (no staging)");
+  const fwh_status st = take_deferred(h);
+  if (st != FWH_OK) return st;
   return h->precision == FWH_FP64
              ? forward_into_scratch_t<double>(h, reinterpret_cast<const double *>(fields), nt,
                                               p_out, s, static_cast<unsigned char *>(scratch),

@@ -44,6 +44,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstring>
+
 #include "fwh_internal.cuh"
 
 namespace fwh {
@@ -147,28 +149,37 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 // Test the phase; a thread whose phase is not complete is suspended until it
-// completes or kSuspendNs pass, so waiting warps do not spin on issue slots.
+// completes or `suspend_ns` pass, so waiting warps do not spin on issue slots.
 constexpr unsigned kSuspendNs = 200000;
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity,
+                                              unsigned suspend_ns = kSuspendNs) {
   unsigned ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(suspend_ns)
       : "memory");
   return ok != 0;
 }
+// Suspend hint of a wait bounded by `limit` clocks: never longer than the bound
+// (about 2 clocks per ns at the SM's clock), so a short bound runs out promptly.
+__device__ __forceinline__ unsigned suspend_for(long long limit) {
+  return limit >= 2LL * kSuspendNs ? kSuspendNs : (unsigned)(limit >> 1);
+}
 // Bounded wait: false on timeout (flag raised) or when another warp aborted.
+// `limit` is the bound in SM clocks (<= 0: kWaitCycles).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int *err,
-                                          volatile int *abort) {
-  if (mbar_try_wait(bar, parity)) return true;
+                                          volatile int *abort, long long limit = 0) {
+  if (limit <= 0) limit = kWaitCycles;
+  const unsigned ns = suspend_for(limit);
+  if (mbar_try_wait(bar, parity, ns)) return true;
   const long long t0 = clock64();
   for (;;) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait(bar, parity, ns)) return true;
     if (*abort) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       atomicOr(err, kErrTimeout);
       *abort = 1;
       return false;
@@ -179,16 +190,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int *e
 // while the compute warps work it takes almost no issue slots from the warps
 // that share its SM sub-partition.
 __device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, unsigned parity, int *err,
-                                                volatile int *abort) {
-  if (mbar_try_wait(bar, parity)) return true;
+                                                volatile int *abort, long long limit = 0) {
+  if (limit <= 0) limit = kWaitCycles;
+  const unsigned sus = suspend_for(limit);
+  if (mbar_try_wait(bar, parity, sus)) return true;
   const long long t0 = clock64();
   unsigned ns = 64;
   for (;;) {
     __nanosleep(ns);
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait(bar, parity, sus)) return true;
     if (ns < 512) ns <<= 1;
     if (*abort) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       atomicOr(err, kErrTimeout);
       *abort = 1;
       return false;
@@ -405,6 +418,7 @@ struct PipeState {
   volatile int *abort;
   int *released;  // in-line producer: per-stage count of warps done with it
   int *issued;    // in-line producer: steps issued so far (for the drain)
+  const void *tmap;  // tensor map of the X rows being streamed
 };
 
 // Threads per CTA: compute warps, plus the producer warp of the TMA pipeline
@@ -426,7 +440,7 @@ __device__ __forceinline__ void issue_step(const FwdArgs<T> &a, const Item<T, NW
   unsigned char *dst = ps.stage0 + (size_t)slot * ps.stage_bytes;
   mbar_expect_tx(bar, ps.x_bytes + cbytes);
   const int row = p * a.ntp + k0;  // tensor rows are 128 bytes
-  tma_load_2d(dst, a.tmX, 0, sizeof(T) == 4 ? row >> 1 : row, bar);
+  tma_load_2d(dst, ps.tmap, 0, sizeof(T) == 4 ? row >> 1 : row, bar);
   bulk_load(dst + ps.x_bytes, a.coef + ((size_t)p * a.O + it.o_begin) * kRec, cbytes, bar);
 }
 
@@ -468,13 +482,14 @@ __device__ __forceinline__ void produce_item(const FwdArgs<T> &a, const Item<T, 
   for (int idx = 0; idx < nsteps; ++idx, ++step) {
     if (*ps.abort) return;
     if (idx + lead < nsteps) prefetch_next();
-    if (step >= (unsigned)ps.nst && !mbar_wait_sleep(&ps.empty[s], ph ^ 1u, a.err, ps.abort))
+    if (step >= (unsigned)ps.nst &&
+        !mbar_wait_sleep(&ps.empty[s], ph ^ 1u, a.err, ps.abort, a.wait_cycles))
       return;
     unsigned char *dst = ps.stage0 + (size_t)s * ps.stage_bytes;
     mbar_expect_tx(&ps.full[s], ps.x_bytes + cbytes);
     // tensor rows are 128 bytes: two FP32 samples or one FP64 sample
     const int row = (it.p_begin + cp) * a.ntp + it.k_begin + ck * CH;
-    tma_load_2d(dst, a.tmX, 0, sizeof(T) == 4 ? row >> 1 : row, &ps.full[s]);
+    tma_load_2d(dst, ps.tmap, 0, sizeof(T) == 4 ? row >> 1 : row, &ps.full[s]);
     bulk_load(dst + ps.x_bytes, src_c(cp), cbytes, &ps.full[s]);
     if (++cp == np) {
       cp = 0;
@@ -500,7 +515,7 @@ __device__ __forceinline__ void consume_item(const FwdArgs<T> &a, const Item<T, 
     for (int p = it.p_begin; p < it.p_end; ++p, ++step) {
       const int s = (int)(step % (unsigned)ps.nst);
       const unsigned ph = (step / (unsigned)ps.nst) & 1u;
-      if (!mbar_wait(&ps.full[s], ph, a.err, ps.abort)) return;
+      if (!mbar_wait(&ps.full[s], ph, a.err, ps.abort, a.wait_cycles)) return;
       const unsigned char *stg = ps.stage0 + (size_t)s * ps.stage_bytes;
       T x[TK][kRec];
 #pragma unroll
@@ -633,7 +648,7 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
   int j = 0;  // in-item step index
   for (int k0 = it.k_begin; k0 < it.k_end; k0 += CH) {
     for (int p = it.p_begin; p < it.p_end; ++p, ++step, ++j) {
-      if (!mbar_wait(&ps.full[s], ph, a.err, ps.abort)) return;
+      if (!mbar_wait(&ps.full[s], ph, a.err, ps.abort, a.wait_cycles)) return;
       const unsigned stg = stage_token(stage0 + s * ps.stage_bytes);
       float X[NP][2][kRec];  // [pair row][sample s, s + 32][value]
 #pragma unroll
@@ -722,7 +737,9 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
   flush_tail<float, CH, NW>(a, it, w, wwin, s_i0max);
 }
 
-// Wait (bounded) until every copy the producer issued has landed.
+// Wait until every copy the producer issued has landed, always with the full
+// bound (never the handle's test bound): the CTA must not exit while a copy
+// into its shared memory is in flight.
 __device__ __forceinline__ void drain_copies(const PipeState &ps, unsigned step, int *err) {
   const unsigned first = step > (unsigned)ps.nst ? step - (unsigned)ps.nst : 0u;
   volatile int never = 0;
@@ -776,10 +793,11 @@ struct MinBlocks {
 };
 
 template <typename T, int TK, int NW, int PIPE, int ACC>
-__device__ __forceinline__ void forward_cta(const FwdArgs<T> &a, int nst) {
+__device__ __forceinline__ void forward_cta(const FwdArgs<T> &a, const void *tmap, int nst) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int st[NW * kMaxObsPerWarp];
   if constexpr (PIPE == 0) {
+    (void)tmap;
     process_item_direct<T, TK, NW>(a, blockIdx.x, reinterpret_cast<T *>(smem_raw), st);
   } else if constexpr (PIPE == 2) {
     static_assert(sizeof(T) == 4 && ACC >= 3, "the in-line producer serves the FP32 consumer");
@@ -790,6 +808,7 @@ __device__ __forceinline__ void forward_cta(const FwdArgs<T> &a, int nst) {
     PipeState ps;
     unsigned char *wbase = pipe_setup<T, TK, NW>(smem_raw, a.obs_per_cta, nst, bars,
                                                  &abort_flag, ps, released, &issued);
+    ps.tmap = tmap;
     const int w = threadIdx.x >> 5;
     const Item<T, NW> it(a, blockIdx.x, w);
     if (threadIdx.x == 0) {  // fill the ring
@@ -809,6 +828,7 @@ __device__ __forceinline__ void forward_cta(const FwdArgs<T> &a, int nst) {
     PipeState ps;
     unsigned char *wbase = pipe_setup<T, TK, NW>(smem_raw, a.obs_per_cta, nst, bars,
                                                  &abort_flag, ps);
+    ps.tmap = tmap;
     const int w = threadIdx.x >> 5;
     unsigned step = 0;
     if (w == NW) {
@@ -832,15 +852,16 @@ __device__ __forceinline__ void forward_cta(const FwdArgs<T> &a, int nst) {
 
 template <typename T, int TK, int NW, int PIPE, int ACC>
 __global__ void __launch_bounds__((cta_threads<NW, PIPE>()), (MinBlocks<TK, NW, PIPE>::v))
-    k_forward(FwdArgs<T> a, int nst) {
-  forward_cta<T, TK, NW, PIPE, ACC>(a, nst);
+    k_forward(FwdArgs<T> a, const __grid_constant__ CUtensorMap tm, int nst) {
+  forward_cta<T, TK, NW, PIPE, ACC>(a, &tm, nst);
 }
 
 // Same CTA program for the long-sample-block shapes (TK = 8), which need
 // about 190 registers: capped at 200 so that two CTAs still share an SM.
 template <typename T, int TK, int NW, int PIPE, int ACC>
-__global__ void __maxnreg__(200) k_forward_wide(FwdArgs<T> a, int nst) {
-  forward_cta<T, TK, NW, PIPE, ACC>(a, nst);
+__global__ void __maxnreg__(200) k_forward_wide(FwdArgs<T> a,
+                                                const __grid_constant__ CUtensorMap tm, int nst) {
+  forward_cta<T, TK, NW, PIPE, ACC>(a, &tm, nst);
 }
 
 // Persistent form: CTAs pull work items of several surfaces from one queue.
@@ -877,6 +898,7 @@ __device__ __forceinline__ void forward_batch_cta(const FwdArgs<T> *args, const 
     }
     const FwdArgs<T> a = args[lo];
     const int li = item - item_prefix[lo];
+    ps.tmap = a.tmX;  // each surface's descriptor lives in device memory
     if constexpr (PIPE == 0) {
       process_item_direct<T, TK, NW>(a, li, reinterpret_cast<T *>(smem_raw), st);
     } else if constexpr (PIPE == 2) {
@@ -973,7 +995,8 @@ size_t smem_for(const FwdConfig &c, int obs_per_cta) {
 }
 
 template <typename T, int TK, int NW, int PIPE, int ACC>
-cudaError_t launch_one(const FwdArgs<T> &a, const FwdConfig &c, cudaStream_t s) {
+cudaError_t launch_one(const FwdArgs<T> &a, const CUtensorMap &tm, const FwdConfig &c,
+                       cudaStream_t s) {
   const size_t smem = smem_for<T>(c, a.obs_per_cta);
   auto kern = c.wide ? k_forward_wide<T, TK, NW, PIPE, ACC> : k_forward<T, TK, NW, PIPE, ACC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -982,7 +1005,7 @@ cudaError_t launch_one(const FwdArgs<T> &a, const FwdConfig &c, cudaStream_t s) 
   if (a.seg_lo < 0 || a.seg_cnt < 1 || a.seg_lo + a.seg_cnt > a.n_segs) return cudaErrorInvalidValue;
   const int items = a.nsets * a.n_obs_groups * a.seg_cnt;
   if (items <= 0) return cudaSuccess;
-  kern<<<items, cta_threads<NW, PIPE>(), smem, s>>>(a, c.stages);
+  kern<<<items, cta_threads<NW, PIPE>(), smem, s>>>(a, tm, c.stages);
   return cudaGetLastError();
 }
 
@@ -1065,9 +1088,15 @@ bool encode_x_tensor_map(void *out128, const void *X, unsigned long long rows, b
   } while (0)
 
 template <typename T>
-cudaError_t launch_forward(const FwdArgs<T> &a, int cfg, cudaStream_t s) {
+cudaError_t launch_forward(const FwdArgs<T> &a, const void *tmap128, int cfg, cudaStream_t s) {
   const FwdConfig c = fwd_config(sizeof(T) == 8, cfg);
-#define FWH_CALL_ONE(TT, TK, NW, PIPE, ACC) launch_one<TT, TK, NW, PIPE, ACC>(a, c, s)
+  // the X descriptor travels as a kernel parameter (no device copy to make)
+  CUtensorMap tm;
+  if (tmap128)
+    memcpy(&tm, tmap128, sizeof tm);
+  else
+    memset(&tm, 0, sizeof tm);
+#define FWH_CALL_ONE(TT, TK, NW, PIPE, ACC) launch_one<TT, TK, NW, PIPE, ACC>(a, tm, c, s)
   FWH_DISPATCH(T, c, FWH_CALL_ONE);
 #undef FWH_CALL_ONE
 }
@@ -1122,8 +1151,10 @@ template cudaError_t launch_plan<float>(float *, const int *, int, int, int, int
                                         cudaStream_t);
 template cudaError_t launch_plan<double>(double *, const int *, int, int, int, int *, int *,
                                          cudaStream_t);
-template cudaError_t launch_forward<float>(const FwdArgs<float> &, int, cudaStream_t);
-template cudaError_t launch_forward<double>(const FwdArgs<double> &, int, cudaStream_t);
+template cudaError_t launch_forward<float>(const FwdArgs<float> &, const void *, int,
+                                           cudaStream_t);
+template cudaError_t launch_forward<double>(const FwdArgs<double> &, const void *, int,
+                                            cudaStream_t);
 template cudaError_t launch_forward_batch<float>(const FwdArgs<float> *, const int *, int, int,
                                                  int *, int, int, cudaStream_t);
 template cudaError_t launch_forward_batch<double>(const FwdArgs<double> *, const int *, int,

@@ -124,7 +124,29 @@ __global__ void __launch_bounds__(128) k_coef(GeomArgs a, T *coef) {
   }
 }
 
+// Observer window length N_o = floor((t_end - t_start)/dt) + 1 (Eqs. t_start,
+// t_end), clamped to [0, nt]: every operation rounded on its own, as the
+// host's planner computes it (no fused multiply-add), so both agree exactly.
+__global__ void k_nvalid(const double *Rmax, const double *Rmin, int O, double mach, double dt,
+                         int nt, int *n_valid) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= O) return;
+  const double tau_max = __dmul_rn((double)(nt - 1), dt);
+  const double ts = __dmul_rn(mach, Rmax[o]);
+  const double te = __dadd_rn(tau_max, __dmul_rn(mach, Rmin[o]));
+  double v = __dadd_rn(floor(__ddiv_rn(__dsub_rn(te, ts), dt)), 1.0);
+  v = fmax(0.0, fmin((double)nt, v));
+  n_valid[o] = (int)v;
+}
+
 }  // namespace
+
+cudaError_t launch_nvalid(const double *Rmax, const double *Rmin, int O, double mach, double dt,
+                          int nt, int *n_valid, cudaStream_t s) {
+  if (O <= 0) return cudaSuccess;
+  k_nvalid<<<(O + 127) / 128, 128, 0, s>>>(Rmax, Rmin, O, mach, dt, nt, n_valid);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_window(const GeomArgs &a, cudaStream_t s) {
   if (a.O <= 0) return cudaSuccess;

@@ -76,7 +76,8 @@ struct PrepArgs {
 
 template <typename T>
 struct FwdArgs {
-  const void *tmX;      // device CUtensorMap over X as [P*ntp rows][16] (TMA pipeline)
+  const void *tmX;      // batched form: device CUtensorMap over X as [P*ntp rows][16]
+                        // (single launches take the descriptor as a kernel parameter)
   const T *X;           // [P][ntp][16]
   const T *coef;        // [P][O][16]
   double *p_out;        // [O][nt]
@@ -90,6 +91,7 @@ struct FwdArgs {
   int seg_len, n_segs;
   int seg_lo, seg_cnt;  // this launch covers time segments [seg_lo, seg_lo + seg_cnt)
   int win;              // window slots per observer
+  long long wait_cycles; // bound of each pipeline wait in SM clocks (the handle's limit)
 };
 
 template <typename T>
@@ -120,6 +122,9 @@ struct PrepAdjArgs {
 
 // ---- launchers (defined in the .cu files) --------------------------------
 cudaError_t launch_window(const GeomArgs &a, cudaStream_t s);
+// N_o per observer (Eq. t_end) from R_max / R_min, rounded as the host does.
+cudaError_t launch_nvalid(const double *Rmax, const double *Rmin, int O, double mach, double dt,
+                          int nt, int *n_valid, cudaStream_t s);
 template <typename T>
 cudaError_t launch_coef(const GeomArgs &a, T *coef, cudaStream_t s);
 cudaError_t upload_pivots(cudaStream_t s);
@@ -155,8 +160,11 @@ bool encode_x_tensor_map(void *out128, const void *X, unsigned long long rows, b
                          int box_rows);
 int fwd_num_configs(bool fp64);
 FwdConfig fwd_config(bool fp64, int idx);
+// tmap128: host copy of the X tensor map (128 bytes) for TMA configs, passed
+// to the kernel as a parameter; may be null for direct-load configs.
 template <typename T>
-cudaError_t launch_forward(const FwdArgs<T> &a, int cfg_idx, cudaStream_t s);
+cudaError_t launch_forward(const FwdArgs<T> &a, const void *tmap128, int cfg_idx,
+                           cudaStream_t s);
 // Planner kernel: per (panel set, observer) the largest shift i0max into
 // i0max_tab and, per record, the window offset i0max - i0 clamped to
 // [0, slack] (slack = win - chunk - 1) into slot 13; a set whose shifts span

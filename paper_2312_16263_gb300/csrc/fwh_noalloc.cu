@@ -3,12 +3,12 @@
 //
 // Who needs this: code that must not call cudaMalloc/cudaFree (or any
 // allocator, torch's caching allocator included) while it runs -- for
-// example a host callback or a real-time loop whose memory was budgeted up
-// front, a process whose device memory is owned by another framework that
-// forbids allocations during a step, or an embedding where an allocation
-// could synchronise the device at the wrong moment.  Such a caller sets the
-// handle up earlier (fwh_create and fwh_set_observers do allocate) and then
-// calls fwh_forward_noalloc in its steady state.
+// example a real-time loop whose memory was budgeted up front, a process whose
+// device memory is owned by another framework that forbids allocations during
+// a step, or an embedding where an allocation could synchronise the device at
+// the wrong moment.  Such a caller sets the handle up earlier (fwh_create and
+// fwh_set_observers do allocate) and then calls fwh_forward_noalloc in its
+// steady state.  The call copies nothing from host memory either.
 //
 // Limits and sharing: the array is kStaticScratchBytes (64 MiB) and every
 // GPU that loads this library reserves it until the process exits.  All
