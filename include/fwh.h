@@ -192,10 +192,12 @@ fwh_status fwh_check(fwh_handle h, void *stream);
  * runs out raises FWH_ERR_TIMEOUT through the device check, the kernel stops
  * issuing copies, waits (always with the default bound) for those in flight
  * and returns; p_out of that call is then incomplete, and the handle stays
- * usable.  Meant for testing that error path: a bound of a few cycles runs
- * out on any forward call.  Errors: FWH_ERR_ARG for a negative bound.
+ * usable.  withhold_copies != 0 is for testing that error path: the copy
+ * pipeline then issues no copies at all, so every stage wait runs out after
+ * `cycles` (nothing is in flight when the kernel returns).
+ * Errors: FWH_ERR_ARG for a negative bound.
  */
-fwh_status fwh_set_wait_limit(fwh_handle h, int64_t cycles);
+fwh_status fwh_set_wait_limit(fwh_handle h, int64_t cycles, int withhold_copies);
 
 /*
  * Forward pass that allocates no device memory.  The paper has no

@@ -128,9 +128,11 @@ class FWH:
     def set_tile_config(self, idx: int):
         _abi.check(self.lib.fwh_set_tile_config(self.h, int(idx)), self.h)
 
-    def set_wait_limit(self, cycles: int = 0):
-        """Bound (SM clocks) of the forward pipeline's waits; 0 = default."""
-        _abi.check(self.lib.fwh_set_wait_limit(self.h, int(cycles)), self.h)
+    def set_wait_limit(self, cycles: int = 0, withhold_copies: bool = False):
+        """Bound (SM clocks) of the forward pipeline's waits; 0 = default.
+        withhold_copies (testing): issue no copies, so every wait runs out."""
+        _abi.check(self.lib.fwh_set_wait_limit(self.h, int(cycles), int(bool(withhold_copies))),
+                   self.h)
 
     def set_timing(self, enable: bool = True):
         _abi.check(self.lib.fwh_set_timing(self.h, int(bool(enable))), self.h)

@@ -70,6 +70,7 @@ struct fwh_ctx {
   long long tmap_rows = 0;
   bool tmap_dev_ok = false;      // the device copy equals the host descriptor
   long long wait_limit = 0;      // bound of the forward pipeline waits (0: default)
+  int withhold = 0;              // testing: the forward pipeline issues no copies
   // deferred device check: each call with device outputs copies the error flag
   // into pinned host memory; the next call (or fwh_check) reads it
   int *h_err = nullptr;
@@ -241,10 +242,11 @@ fwh_status plan(fwh_handle h, const FwdConfig &c, cudaStream_t s) {
   if (h->precision == FWH_FP64)
     CK(h, launch_plan<double>(reinterpret_cast<double *>(h->coef.p),
                               reinterpret_cast<const int *>(h->sets.p), nsets, (int)h->O, smax,
-                              reinterpret_cast<int *>(h->imax.p), h->d_err, s));
+                              0, reinterpret_cast<int *>(h->imax.p), h->d_err, s));
   else
     CK(h, launch_plan<float>(reinterpret_cast<float *>(h->coef.p),
                              reinterpret_cast<const int *>(h->sets.p), nsets, (int)h->O, smax,
+                             (c.win / 2) * (int)sizeof(float),
                              reinterpret_cast<int *>(h->imax.p), h->d_err, s));
   h->plan_win = c.win;
   h->plan_ch = ch;
@@ -381,6 +383,7 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
   FwdArgs<T> fa{};
   fa.tmX = nullptr;
   fa.wait_cycles = h->wait_limit;
+  fa.withhold = h->withhold;
   fa.X = pa.X;
   fa.coef = reinterpret_cast<const T *>(h->coef.p);
   fa.p_out = d_pout;
@@ -932,10 +935,11 @@ fwh_status fwh_autotune(fwh_handle h, int64_t nt, int *chosen, void *stream) {
   return plan_default(h);
 }
 
-fwh_status fwh_set_wait_limit(fwh_handle h, int64_t cycles) {
+fwh_status fwh_set_wait_limit(fwh_handle h, int64_t cycles, int withhold_copies) {
   if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
   if (cycles < 0) return fail(h, FWH_ERR_ARG, "wait limit must be >= 0");
   h->wait_limit = cycles;
+  h->withhold = withhold_copies != 0;
   drop_graphs(h);
   return FWH_OK;
 }
@@ -1041,6 +1045,7 @@ fwh_status batch_build(int n, const fwh_handle *hs, const void *const *fields,
     FwdArgs<T> &fa = args[i];
     fa.tmX = h->tmap.p;
     fa.wait_cycles = h0->wait_limit;
+    fa.withhold = h0->withhold;
     fa.X = reinterpret_cast<const T *>(h->X.p);
     fa.coef = reinterpret_cast<const T *>(h->coef.p);
     fa.p_out = p_out[i];
@@ -1145,6 +1150,7 @@ extern "C" fwh_status fwh_batch_forward(int n, const fwh_handle *hs, const void 
   }
   key.push_back((uintptr_t)(h0->cfg + 1));
   key.push_back((uintptr_t)h0->wait_limit);
+  key.push_back((uintptr_t)h0->withhold);
   if (!h0->side) {
     CK(h0, cudaStreamCreateWithFlags(&h0->side, cudaStreamNonBlocking));
     CK(h0, cudaEventCreateWithFlags(&h0->bev[0], cudaEventDisableTiming));
@@ -1241,6 +1247,7 @@ fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, d
   FwdArgs<T> fa{};
   fa.tmX = nullptr;
   fa.wait_cycles = h->wait_limit;
+  fa.withhold = h->withhold;
   fa.X = d_X;
   fa.coef = reinterpret_cast<const T *>(h->coef.p);
   fa.p_out = d_pout;

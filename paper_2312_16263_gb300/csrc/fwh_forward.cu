@@ -237,7 +237,7 @@ template <> __device__ __forceinline__ double int_as_rec<double>(int v) { return
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_plan(T *coef, const int *set_begin, int O, int slack,
-                                              int *i0max_tab, int *err) {
+                                              int half_bytes, int *i0max_tab, int *err) {
   const int sidx = blockIdx.x;
   const int pb = set_begin[sidx], pe = set_begin[sidx + 1];
   for (int o = threadIdx.x; o < O; o += blockDim.x) {
@@ -253,6 +253,11 @@ __global__ void __launch_bounds__(128) k_plan(T *coef, const int *set_begin, int
       T *rec = coef + ((size_t)p * O + o) * kRec;
       const int off = min(hi - rec_i0_of<T>(rec[slot::i0]), slack);
       rec[slot::off] = int_as_rec<T>(off);
+      if (sizeof(T) == 4) {  // split window: slot x in half x & 1, word x >> 1
+        const int x = off + 1, r = x & 1, q = x >> 1;
+        rec[slot::w0] = int_as_rec<T>(r * half_bytes + 4 * q);
+        rec[slot::w1] = int_as_rec<T>((1 - r) * half_bytes + 4 * (q + r));
+      }
     }
   }
 }
@@ -466,6 +471,7 @@ __device__ __forceinline__ void produce_item(const FwdArgs<T> &a, const Item<T, 
   auto src_c = [&](int pp) {
     return a.coef + ((size_t)(it.p_begin + pp) * a.O + it.o_begin) * kRec;
   };
+  if (a.withhold) return;  // testing: no copies, so every consumer wait runs out
   int fp = 0, fk = 0;  // prefetch cursor (panel offset, chunk)
   auto prefetch_next = [&]() {
     prefetch_l2(src_x(fp, fk), ps.x_bytes);
@@ -537,30 +543,33 @@ __device__ __forceinline__ void consume_item(const FwdArgs<T> &a, const Item<T, 
 }
 
 // ---- FP32 consumer (mixed precision) ----------------------------------------
-// FP32 X rows pair the samples j and j + 32 of each 64-sample block, so the
-// 16-byte chunk c of pair row pi = 32 b + j holds (x_k[2c], x_k+32[2c],
-// x_k[2c+1], x_k+32[2c+1]), k = 64 b + j: one swizzled row read per lane
-// gives both samples' series.  Lane l owns pair rows pi = l + 32 t of a chunk
-// (samples s = 64 t + l and s + 32) and forms, per observer, G = sum_q c_q X_q
-// and M likewise on the moments, u = a G + cc M (left-node part) and v = b G
-// + dd M (right-node part), all as scalar FMAs (a packed fma.rn.f32x2 takes
-// two issue cycles, so it buys no throughput over FFMA here).  Sample s adds
-// u_s to window slot 1 + s + off and v_s to slot s + off, so slot 1 + s + off
-// receives u_s + v_s+1: lane l takes v_s+1 from lane l + 1 (lane 31 from lane
-// 0's other sample, or from lane 0 of block t + 1) and updates the slots of
-// its two samples, 32 apart, with 32-bit read-modify-writes whose old value
-// enters the u FMA.  Consecutive lanes touch consecutive slots: no bank
-// conflicts, and no dependence of the code path on the shift.  The slot below
-// the chunk (v_0) is added by lane 0 separately.  Within one (panel,
-// observer) no two lanes touch the same slot; one __syncwarp per panel
-// orders the next panel's shifted updates.
-// Shared-space accesses by 32-bit address (the packed consumer addresses the
-// stage ring and its windows explicitly, so no generic-address arithmetic).
-__device__ __forceinline__ int lds_s32(unsigned addr) {
-  int v;
-  asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
-  return v;
-}
+// FP32 X rows pair the consecutive samples 2r and 2r + 1 of each 64-sample
+// block, so the 16-byte chunk c of pair row r holds (x_k[2c], x_k+1[2c],
+// x_k[2c+1], x_k+1[2c+1]), k = 64 b + 2 r: one swizzled row read per lane
+// gives both samples' series.  Lane l owns pair rows l + 32 t of a chunk
+// (samples s = 64 t + 2 l and s + 1) and forms, per observer, G = sum_q c_q
+// X_q and M likewise on the moments, all as scalar FMAs (a packed
+// fma.rn.f32x2 takes two issue cycles, so it buys no throughput over FFMA).
+// Sample s adds a G + cc M (left spline node) to window slot 1 + s + off and
+// b G + dd M (right node) to slot s + off, so slot 1 + s + off receives
+// a G_s + cc M_s + b G_s+1 + dd M_s+1.  For the first sample of a pair both
+// nodes are the lane's own: the old slot value enters a chain of four FMAs.
+// For the second, v = b G + dd M of the next sample comes from lane l + 1
+// (lane 31: lane 0's pair of block t + 1), one shuffle per pair; the last
+// block's lane 31 has no successor in the chunk, and the slot below the
+// chunk (v of sample 0) is added by lane 0, so the chunk-crossing node is
+// split between two chunks exactly once.
+//
+// Split windows: slot x of an observer's window lives in half x & 1 at word
+// x >> 1, so the two slots of a lane's pair sit in different halves and 32
+// lanes touch 32 consecutive words of one half per access: conflict-free for
+// every offset.  The planner writes each record's two byte offsets (slots 14,
+// 15: the words of slots off + 1 and off + 2 relative to the window), so the
+// hot loop adds them to the lane's base and never branches on the shift.
+// Within one (panel, observer) no two lanes touch the same slot; one
+// __syncwarp per panel orders the next panel's shifted updates.
+// Shared-space accesses by 32-bit address (the consumer addresses the stage
+// ring and its windows explicitly, so no generic-address arithmetic).
 __device__ __forceinline__ float lds_f32(unsigned addr) {
   float v;
   asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
@@ -568,20 +577,6 @@ __device__ __forceinline__ float lds_f32(unsigned addr) {
 }
 __device__ __forceinline__ void sts_f32(unsigned addr, float v) {
   asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
-}
-// Read-modify-write add to one shared float by the lanes whose `on` is
-// nonzero, predicated (no branch).  Not atomic: the caller guarantees that no
-// other lane touches the address at the same time (a shared-memory atomic
-// here stalls the warp's later shared accesses).
-__device__ __forceinline__ void add_f32_if(unsigned addr, float v, unsigned on) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\t.reg .f32 t;\n\t"
-      "setp.ne.u32 q, %2, 0;\n\t"
-      "@q ld.shared.f32 t, [%0];\n\t"
-      "@q add.f32 t, t, %1;\n\t"
-      "@q st.shared.f32 [%0], t;\n\t}" ::"r"(addr),
-      "f"(v), "r"(on)
-      : "memory");
 }
 
 // Loads of stage data (X rows, records): not volatile, so the compiler may
@@ -594,9 +589,9 @@ __device__ __forceinline__ float4 lds_v4f32(unsigned addr) {
       : "r"(addr));
   return v;
 }
-__device__ __forceinline__ int lds_s32_stage(unsigned addr) {
-  int v;
-  asm("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr));
+__device__ __forceinline__ uint2 lds_v2u32_stage(unsigned addr) {
+  uint2 v;
+  asm("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
   return v;
 }
 // The stage address as an opaque value produced after the barrier wait.
@@ -605,21 +600,92 @@ __device__ __forceinline__ unsigned stage_token(unsigned addr) {
   asm volatile("mov.u32 %0, %1;" : "=r"(r) : "r"(addr) : "memory");
   return r;
 }
+// x + (the value of the lane above, if there is one): the last lane keeps x.
+__device__ __forceinline__ float add_from_lane_above(float x, float v) {
+  float r;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t.reg .f32 t;\n\t"
+      "shfl.sync.down.b32 t|p, %2, 1, 0x1f, 0xffffffff;\n\t"
+      "mov.f32 %0, %1;\n\t"
+      "@p add.f32 %0, %1, t;\n\t}"
+      : "=f"(r)
+      : "f"(x), "f"(v));
+  return r;
+}
 
-// The first 14 slots of one FP32 record: c0..c7, a, b, cc, dd, i0, off.
+// The slots of one FP32 record that the consumer reads: c0..c7, a, b, cc, dd
+// and the two window byte offsets (slots 14, 15).
 struct Coef {
   float c[8], wa, wb, wcc, wdd;
-  int off;
+  unsigned r0, r1;
 };
 __device__ __forceinline__ void lds_coef(unsigned rec, Coef &k) {
   static_assert(slot::c == 0 && slot::a == 8 && slot::b == 9 && slot::cc == 10 &&
-                    slot::dd == 11 && slot::off == 13,
-                "record read as three 16-byte groups and one word");
+                    slot::dd == 11 && slot::w0 == 14 && slot::w1 == 15,
+                "record read as three 16-byte groups and one 8-byte pair");
   const float4 c0 = lds_v4f32(rec), c1 = lds_v4f32(rec + 16), w = lds_v4f32(rec + 32);
+  const uint2 r = lds_v2u32_stage(rec + 4 * slot::w0);
   k.c[0] = c0.x; k.c[1] = c0.y; k.c[2] = c0.z; k.c[3] = c0.w;
   k.c[4] = c1.x; k.c[5] = c1.y; k.c[6] = c1.z; k.c[7] = c1.w;
   k.wa = w.x; k.wb = w.y; k.wcc = w.z; k.wdd = w.w;
-  k.off = lds_s32_stage(rec + 4 * slot::off);
+  k.r0 = r.x;
+  k.r1 = r.y;
+}
+
+// Flush the first CH (complete) bins of every split window to p_out and slide.
+template <int CH, int NW>
+__device__ __forceinline__ void flush_slide_split(const FwdArgs<float> &a,
+                                                  const Item<float, NW> &it, int w, float *wwin,
+                                                  const int *s_i0max, int k0) {
+  const int lane = threadIdx.x & 31;
+  const int H = a.win >> 1;
+  for (int m = 0; m < it.nobs; ++m) {
+    const int o = it.o_begin + w + NW * m;
+    float *wm = wwin + (size_t)m * a.win;
+    const int wbase = k0 - s_i0max[m] - 1;
+    const int nvalid = a.n_valid[o];
+    double *po = a.p_out + (size_t)o * a.nt;
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf)
+      for (int q = lane; q < CH / 2; q += 32) {
+        const int bin = wbase + 2 * q + hf;
+        const float v = wm[hf * H + q];
+        if (bin >= 0 && bin < nvalid && v != 0.f) atomic_add_f64(po + bin, (double)v);
+      }
+    __syncwarp();
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf)  // H - CH/2 <= CH/2: no overlap
+      for (int q = lane; q < H - CH / 2; q += 32) wm[hf * H + q] = wm[hf * H + CH / 2 + q];
+    __syncwarp();
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf)
+      for (int q = H - CH / 2 + lane; q < H; q += 32) wm[hf * H + q] = 0.f;
+    __syncwarp();
+  }
+}
+
+// Segment end: the remaining split window holds partial bins of the next segment.
+template <int CH, int NW>
+__device__ __forceinline__ void flush_tail_split(const FwdArgs<float> &a,
+                                                 const Item<float, NW> &it, int w, float *wwin,
+                                                 const int *s_i0max) {
+  const int lane = threadIdx.x & 31;
+  const int H = a.win >> 1;
+  for (int m = 0; m < it.nobs; ++m) {
+    const int o = it.o_begin + w + NW * m;
+    const float *wm = wwin + (size_t)m * a.win;
+    const int wbase = it.k_end - s_i0max[m] - 1;
+    const int nvalid = a.n_valid[o];
+    double *po = a.p_out + (size_t)o * a.nt;
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf)
+      for (int q = lane; q < H - CH / 2; q += 32) {
+        const int bin = wbase + 2 * q + hf;
+        const float v = wm[hf * H + q];
+        if (bin >= 0 && bin < nvalid && v != 0.f) atomic_add_f64(po + bin, (double)v);
+      }
+  }
+  __syncwarp();
 }
 
 template <int TK, int NW, bool PF, int PIPE>
@@ -633,16 +699,16 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   item_prologue<float, NW>(a, it, w, wwin, s_i0max);
-  // Window of observer m starts at win_s + m * win_b; lane l's slot for its
-  // block-t samples is 1 + 64 t + l (+ 32) + off.
+  // Window of observer m starts at win_s + m * win_b; the record's byte
+  // offsets r0 / r1 locate slots off + 1 / off + 2 of lane 0, block 0, and
+  // block t adds 32 words.
   const unsigned win_b = (unsigned)a.win * 4u;
-  const unsigned win_s = smem_u32(wwin) + (1u + (unsigned)lane) * 4u;
+  const unsigned win_s = smem_u32(wwin) + (unsigned)lane * 4u;
   const unsigned stage0 = smem_u32(ps.stage0);
-  // X pair row pi = lane + 32 t of a stage: 16-byte chunk c at c ^ (lane & 7).
+  // X pair row r = lane + 32 t of a stage: 16-byte chunk c at c ^ (lane & 7).
   const unsigned xrow = (unsigned)lane * 128u;
   const unsigned xswz = ((unsigned)lane & 7u) << 4;
-  const bool last = lane == 31;
-  const unsigned first = lane == 0;
+  const bool first = lane == 0;
   unsigned s = step % (unsigned)ps.nst, ph = (step / (unsigned)ps.nst) & 1u;
   const int nsteps = (it.p_end - it.p_begin) * ((it.k_end - it.k_begin) / CH);
   int j = 0;  // in-item step index
@@ -650,7 +716,7 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
     for (int p = it.p_begin; p < it.p_end; ++p, ++step, ++j) {
       if (!mbar_wait(&ps.full[s], ph, a.err, ps.abort, a.wait_cycles)) return;
       const unsigned stg = stage_token(stage0 + s * ps.stage_bytes);
-      float X[NP][2][kRec];  // [pair row][sample s, s + 32][value]
+      float X[NP][2][kRec];  // [pair row][sample 2r, 2r + 1][value]
 #pragma unroll
       for (int t = 0; t < NP; ++t) {
 #pragma unroll
@@ -671,44 +737,50 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
       for (int m = 0; m < kMaxObsPerWarpF32; ++m) {
         if (m >= it.nobs) break;
         if (!PF) lds_coef(crec + (unsigned)m * NW * RB, k);
-        const unsigned w1 = win_s + (unsigned)m * win_b + (unsigned)k.off * 4u;
-        float u[NP][2], v[NP][2];
-#pragma unroll
-        for (int t = 0; t < NP; ++t)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) u[t][h] = lds_f32(w1 + 256u * t + 128u * h);
+        const unsigned base = win_s + (unsigned)m * win_b;
+        const unsigned A0 = base + k.r0, A1 = base + k.r1;
+        float s0[NP], s1[NP], v0[NP];
 #pragma unroll
         for (int t = 0; t < NP; ++t) {
+          s0[t] = lds_f32(A0 + 128u * t);
+          s1[t] = lds_f32(A1 + 128u * t);
+        }
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float G = k.c[0] * X[t][h][0];
-            float M = k.c[0] * X[t][h][8];
+        for (int t = 0; t < NP; ++t) {
+          float G0 = k.c[0] * X[t][0][0], M0 = k.c[0] * X[t][0][8];
+          float G1 = k.c[0] * X[t][1][0], M1 = k.c[0] * X[t][1][8];
 #pragma unroll
-            for (int q = 1; q < 8; ++q) {
-              G = fmaf(k.c[q], X[t][h][q], G);
-              M = fmaf(k.c[q], X[t][h][8 + q], M);
-            }
-            u[t][h] = fmaf(k.wcc, M, fmaf(k.wa, G, u[t][h]));  // old slot value + u
-            v[t][h] = fmaf(k.wdd, M, k.wb * G);
+          for (int q = 1; q < 8; ++q) {
+            G0 = fmaf(k.c[q], X[t][0][q], G0);
+            M0 = fmaf(k.c[q], X[t][0][8 + q], M0);
+            G1 = fmaf(k.c[q], X[t][1][q], G1);
+            M1 = fmaf(k.c[q], X[t][1][8 + q], M1);
           }
+          // slot of the pair's first sample: both spline nodes are this lane's
+          s0[t] = fmaf(k.wdd, M1, fmaf(k.wb, G1, fmaf(k.wcc, M0, fmaf(k.wa, G0, s0[t]))));
+          // slot of the second: its left node, the right one comes from above
+          s1[t] = fmaf(k.wcc, M1, fmaf(k.wa, G1, s1[t]));
+          // right node of the pair's first sample, for the lane below
+          v0[t] = fmaf(k.wdd, M0, k.wb * G0);
         }
         Coef kn;
         if (PF && m + 1 < it.nobs) lds_coef(crec + (unsigned)(m + 1) * NW * RB, kn);
-        float sv[NP][2];
 #pragma unroll
-        for (int t = 0; t < NP; ++t)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) sv[t][h] = __shfl_sync(0xffffffffu, v[t][h], (lane + 1) & 31);
+        for (int t = 0; t + 1 < NP; ++t) {
+          // lane 0 serves lane 31 with block t + 1's first sample
+          const float x = first ? v0[t + 1] : v0[t];
+          s1[t] += __shfl_sync(0xffffffffu, x, (lane + 1) & 31);
+        }
+        s1[NP - 1] = add_from_lane_above(s1[NP - 1], v0[NP - 1]);
 #pragma unroll
         for (int t = 0; t < NP; ++t) {
-          // v of the sample after each of the lane's two: lane l + 1's, and
-          // for lane 31 lane 0's other sample / lane 0 of the next block
-          const float e0 = last ? sv[t][1] : sv[t][0];
-          const float e1 = last ? (t + 1 < NP ? sv[t + 1 < NP ? t + 1 : t][0] : 0.f) : sv[t][1];
-          sts_f32(w1 + 256u * t, u[t][0] + e0);
-          sts_f32(w1 + 256u * t + 128u, u[t][1] + e1);
+          sts_f32(A0 + 128u * t, s0[t]);
+          sts_f32(A1 + 128u * t, s1[t]);
         }
-        add_f32_if(w1 - 4u, v[0][0], first);  // slot below the chunk (lane 0 only)
+        if (first) {  // the slot below the chunk: right node of sample 0
+          const unsigned ae = A1 - 4u;
+          sts_f32(ae, lds_f32(ae) + v0[0]);
+        }
         if (PF && m + 1 < it.nobs) k = kn;
       }
       __syncwarp();
@@ -717,7 +789,7 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
         if (lane == 0) {
           __threadfence_block();
           const int done = atomicAdd(&ps.released[s], 1) + 1;
-          if (done % NW == 0 && j + ps.nst < nsteps) {
+          if (done % NW == 0 && j + ps.nst < nsteps && !a.withhold) {
             __threadfence_block();
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue_step<float, TK, NW>(a, it, ps, j + ps.nst, s);
@@ -732,9 +804,9 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
         ph ^= 1u;
       }
     }
-    flush_slide<float, CH, NW>(a, it, w, wwin, s_i0max, k0);
+    flush_slide_split<CH, NW>(a, it, w, wwin, s_i0max, k0);
   }
-  flush_tail<float, CH, NW>(a, it, w, wwin, s_i0max);
+  flush_tail_split<CH, NW>(a, it, w, wwin, s_i0max);
 }
 
 // Wait until every copy the producer issued has landed, always with the full
@@ -811,7 +883,7 @@ __device__ __forceinline__ void forward_cta(const FwdArgs<T> &a, const void *tma
     ps.tmap = tmap;
     const int w = threadIdx.x >> 5;
     const Item<T, NW> it(a, blockIdx.x, w);
-    if (threadIdx.x == 0) {  // fill the ring
+    if (threadIdx.x == 0 && !a.withhold) {  // fill the ring
       const int nsteps = (it.p_end - it.p_begin) * ((it.k_end - it.k_begin) / (32 * TK));
       const int n0 = min(nst, nsteps);
       for (int j = 0; j < n0; ++j) issue_step<T, TK, NW>(a, it, ps, j, (unsigned)j);
@@ -904,7 +976,7 @@ __device__ __forceinline__ void forward_batch_cta(const FwdArgs<T> *args, const 
     } else if constexpr (PIPE == 2) {
       if (abort_flag) break;
       const Item<T, NW> it(a, li, w);
-      if (threadIdx.x == 0) {  // fill the ring: every stage is free here
+      if (threadIdx.x == 0 && !a.withhold) {  // fill the ring: every stage is free here
         const int nsteps = (it.p_end - it.p_begin) * ((it.k_end - it.k_begin) / (32 * TK));
         const int n0 = min(nst, nsteps);
         for (int j = 0; j < n0; ++j)
@@ -956,12 +1028,11 @@ __global__ void __maxnreg__(200)
 }
 
 // Candidate tile shapes {pipe, tk, warps, obs_per_warp, win, seg_chunks,
-// stages, acc, wide}.  acc: 0 one sample per lane per block (FP64), 3 two
-// samples 32 apart per lane per block (FP32; its series rows pair those
-// samples, so every FP32 shape is a TMA shape), 4 the same with the next
-// observer's record read ahead.  wide: register cap 200 instead of the launch
-// bounds' occupancy target.  Register use (ptxas, sm_103a): tk 4 shapes 126
-// to 128 (three CTAs of five warps per SM), tk 8 168 (two).
+// stages, acc, wide}.  acc: 0 one sample per lane per block (FP64), 3 a pair
+// of consecutive samples per lane per block with split windows (FP32; its
+// series rows pair those samples, so every FP32 shape is a TMA shape), 4 the
+// same with the next observer's record read ahead.  wide: register cap 200
+// instead of the launch bounds' occupancy target.
 constexpr FwdConfig kCfgF32[] = {
     {1, 4, 4, 9, 224, 4, 3, 3, 0},
     {1, 4, 4, 9, 224, 2, 3, 3, 0},
@@ -1141,16 +1212,16 @@ template cudaError_t forward_batch_occupancy<double>(int, int *);
 
 template <typename T>
 cudaError_t launch_plan(T *coef, const int *set_begin, int nsets, int O, int slack,
-                        int *i0max_tab, int *err, cudaStream_t s) {
+                        int half_bytes, int *i0max_tab, int *err, cudaStream_t s) {
   if (nsets <= 0 || O <= 0) return cudaSuccess;
-  k_plan<T><<<nsets, 128, 0, s>>>(coef, set_begin, O, slack, i0max_tab, err);
+  k_plan<T><<<nsets, 128, 0, s>>>(coef, set_begin, O, slack, half_bytes, i0max_tab, err);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_plan<float>(float *, const int *, int, int, int, int *, int *,
+template cudaError_t launch_plan<float>(float *, const int *, int, int, int, int, int *, int *,
                                         cudaStream_t);
-template cudaError_t launch_plan<double>(double *, const int *, int, int, int, int *, int *,
-                                         cudaStream_t);
+template cudaError_t launch_plan<double>(double *, const int *, int, int, int, int, int *,
+                                         int *, cudaStream_t);
 template cudaError_t launch_forward<float>(const FwdArgs<float> &, const void *, int,
                                            cudaStream_t);
 template cudaError_t launch_forward<double>(const FwdArgs<double> &, const void *, int,

@@ -33,6 +33,9 @@ constexpr int c = 0;    // c0..c7: coefficients of the eight series
 constexpr int a = 8, b = 9, cc = 10, dd = 11;  // interpolation weights
 constexpr int i0 = 12;  // integer shift (bit pattern in FP32 records)
 constexpr int off = 13; // window offset i0max(set) - i0, written by the planner
+// FP32 records: byte offsets, in an observer's split window (slot x in half
+// x & 1, word x >> 1), of the slots off + 1 and off + 2, written by the planner
+constexpr int w0 = 14, w1 = 15;
 }  // namespace slot
 constexpr int kWarp = 32;
 
@@ -92,6 +95,7 @@ struct FwdArgs {
   int seg_lo, seg_cnt;  // this launch covers time segments [seg_lo, seg_lo + seg_cnt)
   int win;              // window slots per observer
   long long wait_cycles; // bound of each pipeline wait in SM clocks (the handle's limit)
+  int withhold;         // testing: the copy pipeline issues no copies (every wait runs out)
 };
 
 template <typename T>
@@ -167,11 +171,13 @@ cudaError_t launch_forward(const FwdArgs<T> &a, const void *tmap128, int cfg_idx
                            cudaStream_t s);
 // Planner kernel: per (panel set, observer) the largest shift i0max into
 // i0max_tab and, per record, the window offset i0max - i0 clamped to
-// [0, slack] (slack = win - chunk - 1) into slot 13; a set whose shifts span
+// [0, slack] (slack = win - chunk - 1) into slot 13 and, for FP32 records,
+// the split-window byte offsets of slots off + 1 and off + 2 into slots 14
+// and 15 (half_bytes: bytes of one window half); a set whose shifts span
 // more than slack raises kErrWindow.
 template <typename T>
 cudaError_t launch_plan(T *coef, const int *set_begin, int nsets, int O, int slack,
-                        int *i0max_tab, int *err, cudaStream_t s);
+                        int half_bytes, int *i0max_tab, int *err, cudaStream_t s);
 
 // Batched persistent forward.
 template <typename T>

@@ -21,7 +21,7 @@
 // right halo wait in shared memory for the back substitution.
 //
 // FP32 (k_prep_iir): the same moments by two first-order recursive filters
-// per 32-sample block (see the kernel), written as whole X tiles.
+// per 64-sample block (see the kernels), written as whole X tiles.
 #include "fwh_internal.cuh"
 
 #include <algorithm>
@@ -95,7 +95,7 @@ struct Integrand {
 };
 
 // Element (sample i, value q) of a panel's FP64 X rows, plain [i][q].  (The
-// FP32 rows, which pair samples 32 apart, are written by k_prep_iir.)
+// FP32 rows, which pair consecutive samples, are written by k_prep_iir.)
 template <typename T> __device__ __forceinline__ size_t xidx(int i, int q);
 template <> __device__ __forceinline__ size_t xidx<double>(int i, int q) {
   return (size_t)i * kRec + q;
@@ -299,7 +299,7 @@ constexpr int kIirRow = 4 * kIirQ;                   // staged row stride (float
 // the moments of its value series, m'_k = (m_{k+1} - m_{k-1}) / (2 dt).  Only
 // the four value series are filtered, and one thread owns one (panel,
 // integrand) over a whole 64-sample block; the four threads of a panel
-// assemble each half row of X (samples r and 32 + r of eight slots) and store
+// assemble each half row of X (the sample pair 2 r, 2 r + 1 of eight slots) and store
 // it as four 16-byte pieces.  Blocks whose filter reach touches a record end
 // are left to k_prep_iir.
 // ---------------------------------------------------------------------------
@@ -432,30 +432,28 @@ __global__ void __launch_bounds__(kIntThreads, 4) k_prep_iir_int(PrepArgs<float>
       auto B = [&](int k) -> float { return bc[k * kIntRow]; };  // k relative to c0
       float y[C + H + 1];
       float yy = 0.f;
-      float Bm = B(-2 - H), B0 = B(-1 - H);
+      float Bmm = B(-3 - H), Bm = B(-2 - H), B0 = B(-1 - H);
 #pragma unroll
       for (int k = -1 - H; k <= C + H - 1; ++k) {
         const float Bp = B(k + 1);
         yy = s6 * (Bp - 2.f * B0 + Bm) + rho * yy;
         if (k >= -1) y[k + 1] = yy;
-        if (k >= C / 2 && k < C) {  // series pairs (k - 32, k)
-          const int r = k - C / 2;
-          put_row(r, 0, (B(r + 1) - B(r - 1)) * inv2h, (Bp - Bm) * inv2h, B(r), B0);
+        if (k >= 1 && k < C && (k & 1)) {  // series of the sample pair (k - 1, k): row (k - 1)/2
+          put_row((k - 1) >> 1, 0, (B0 - Bmm) * inv2h, (Bp - Bm) * inv2h, Bm, B0);
         }
+        Bmm = Bm;
         Bm = B0;
         B0 = Bp;
       }
-      float mh[C / 2 + 2];  // m_k for k = C/2 - 1 .. C
-      float xx = 0.f, m1 = 0.f, m2 = 0.f;
+      float xx = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;  // m1, m2, m3: moments at k + 1, k + 2, k + 3
 #pragma unroll
       for (int k = C + H - 1; k >= -1; --k) {
         xx = y[k + 1] + rho * xx;
         const float mk = -rho * xx;
-        if (k >= C / 2 - 1 && k <= C) mh[k - (C / 2 - 1)] = mk;
-        if (k <= C / 2 - 2) {  // moment pairs of row r = k + 1
-          const int r = k + 1;
-          put_row(r, 8, (m2 - mk) * inv2h, (mh[r + 2] - mh[r]) * inv2h, m1, mh[r + 1]);
+        if (k <= C - 3 && (k & 1)) {  // moments of the sample pair (k + 1, k + 2): row (k + 1)/2
+          put_row((k + 1) >> 1, 8, (m2 - mk) * inv2h, (m3 - m1) * inv2h, m1, m2);
         }
+        m3 = m2;
         m2 = m1;
         m1 = mk;
       }
@@ -492,27 +490,23 @@ __global__ void __launch_bounds__(kIirThreads, 6) k_prep_iir(PrepArgs<float> a) 
   const int c0 = (ei < na ? a.c_lo + ei : a.int_hi + ei - na) * kIirChunk;
   const int p0 = (int)(blockIdx.x / n_edge) * NP;
   const int N = a.nt;
-  // phase B thread: series s, half h (samples c0 + 32 h ..), panel pl; the
-  // two halves of a (panel, series) are lanes 8 apart of one warp
+  // phase B thread: series s, half h (samples c0 + 32 h ..), panel pl
   const int s = tid & 7;
   const int h = (tid >> 3) & 1;
   const int pl = tid >> 4;
   const int pb = p0 + pl;
   const bool live_b = pb < a.P;
-  // X rows of the tile: row r holds samples c0 + r and c0 + 32 + r
-  float *xr = a.X + ((size_t)(live_b ? pb : 0) * a.ntp + c0) * kRec;
-  // lane pair (h = 0, h = 1) stores one float2 {sample c0 + r, c0 + 32 + r}
-  // of slot q: the lower half for the series, the upper for the moments
-  auto put2 = [&](int r, int q, float v, bool mine) {
-    const float o = __shfl_xor_sync(0xffffffffu, v, 8);
-    if (mine && live_b)
-      *reinterpret_cast<float2 *>(xr + r * 2 * kRec + q * 2) =
-          h == 0 ? make_float2(v, o) : make_float2(o, v);
+  // X rows of the tile: row r holds the sample pair c0 + 2 r, c0 + 2 r + 1;
+  // this thread's samples c0 + 32 h + t fill rows 16 h + t / 2
+  float *xr = a.X + ((size_t)(live_b ? pb : 0) * a.ntp + c0 + 32 * h) * kRec;
+  // slot q of the pair (t0, t0 + 1) (t0 even) as one float2
+  auto put2 = [&](int t0, int q, float v0, float v1) {
+    if (live_b) *reinterpret_cast<float2 *>(xr + (t0 >> 1) * 2 * kRec + q * 2) = make_float2(v0, v1);
   };
   if (c0 >= N) {
-    for (int r = 0; r < J; ++r) {
-      put2(r, s, 0.f, h == 0);
-      put2(r, 8 + s, 0.f, h == 1);
+    for (int t = 0; t < J; t += 2) {
+      put2(t, s, 0.f, 0.f);
+      put2(t, 8 + s, 0.f, 0.f);
     }
     return;
   }
@@ -608,13 +602,19 @@ __global__ void __launch_bounds__(kIirThreads, 6) k_prep_iir(PrepArgs<float> a) 
     float y[J + H];
     int k = ks - H;
     float Fm = Fx(k - 1), F0 = Fx(k);
-    float yy = 0.f;
+    float yy = 0.f, held = 0.f;
 #pragma unroll
     for (int t = 0; t < J + 2 * H; ++t, ++k) {
       const float Fp = Fx(k + 1);
       yy = s6 * (Fp - 2.f * F0 + Fm) + rho * yy;
       if (t >= H) y[t - H] = yy;
-      if (t >= H && t < H + J) put2(t - H, s, k < N ? F0 : 0.f, h == 0);
+      if (t >= H && t < H + J) {
+        const float v = k < N ? F0 : 0.f;
+        if (((t - H) & 1) == 0)
+          held = v;
+        else
+          put2(t - H - 1, s, held, v);
+      }
       Fm = F0;
       F0 = Fp;
     }
@@ -622,7 +622,13 @@ __global__ void __launch_bounds__(kIirThreads, 6) k_prep_iir(PrepArgs<float> a) 
 #pragma unroll
     for (int t = J + H - 1; t >= 0; --t) {
       xx = y[t] + rho * xx;
-      if (t < J) put2(t, 8 + s, ks + t < N ? -rho * xx : 0.f, h == 1);
+      if (t < J) {
+        const float v = ks + t < N ? -rho * xx : 0.f;
+        if (t & 1)
+          held = v;
+        else
+          put2(t, 8 + s, v, held);
+      }
     }
   } else {
     // short records (compact code): one-sided derivatives at the first and
@@ -653,12 +659,19 @@ __global__ void __launch_bounds__(kIirThreads, 6) k_prep_iir(PrepArgs<float> a) 
       if (t >= H) ye[t - H] = yy;
     }
 #pragma unroll 1
-    for (int t = 0; t < J; ++t) put2(t, s, ks + t < N ? F(ks + t) : 0.f, h == 0);
-    float xx = 0.f;
+    for (int t = 0; t < J; t += 2)
+      put2(t, s, ks + t < N ? F(ks + t) : 0.f, ks + t + 1 < N ? F(ks + t + 1) : 0.f);
+    float xx = 0.f, held = 0.f;
 #pragma unroll 1
     for (int t = J + H - 1; t >= 0; --t) {
       xx = ye[t] + rho * xx;
-      if (t < J) put2(t, 8 + s, ks + t < N ? -rho * xx : 0.f, h == 1);
+      if (t < J) {
+        const float v = ks + t < N ? -rho * xx : 0.f;
+        if (t & 1)
+          held = v;
+        else
+          put2(t, 8 + s, v, held);
+      }
     }
   }
 }

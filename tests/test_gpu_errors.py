@@ -1,10 +1,11 @@
 """Device-side error reporting of the forward kernel's bounded waits (needs a GPU).
 
-A wait bound of one SM clock (fwh_set_wait_limit) makes the first stage wait
-of every CTA of the copy pipeline run out: the kernel raises the timeout
-flag, stops issuing copies, waits (always with the full bound) for the copies
-already in flight and returns.  Nothing faults or hangs: the copies complete
-and the kernel ends early, leaving p_out incomplete.  The tests check that
+With fwh_set_wait_limit(h, 2000, withhold_copies=1) the copy pipeline issues
+no copies, so the first stage wait of every compute warp waits for a barrier
+that nothing completes and gives up after 2000 SM clocks (about a
+microsecond): the kernel raises the timeout flag and returns.  Nothing faults
+or hangs: no copy is in flight, every wait is bounded, and p_out is left
+incomplete.  The tests check that
 the timeout is reported synchronously by fwh_check, or by the next call when
 the outputs stayed on the device, through the C ABI and the torch wrapper,
 and that the handle computes correct results again afterwards.
@@ -58,7 +59,7 @@ def test_timeout_reported_by_check(dev, prec):
     from paper_2312_16263_gb300 import _abi
     w, s, f = _case(dev, prec)
     out = torch.empty((s.O, w.nt), dtype=torch.float64, device=dev)
-    s.set_wait_limit(1)
+    s.set_wait_limit(2000, withhold_copies=True)
     s.forward(f, out)                         # device output: returns before the check
     st = s.lib.fwh_check(s.h, _abi_stream())
     assert st == _abi.FWH_ERR_TIMEOUT, st
@@ -76,7 +77,7 @@ def test_timeout_reported_on_next_call(dev):
     from paper_2312_16263_gb300._abi import FWHError
     w, s, f = _case(dev, "mixed")
     out = torch.empty((s.O, w.nt), dtype=torch.float64, device=dev)
-    s.set_wait_limit(1)
+    s.set_wait_limit(2000, withhold_copies=True)
     s.forward(f, out)
     torch.cuda.synchronize()                  # the flag copy has landed
     s.set_wait_limit(0)
@@ -88,7 +89,7 @@ def test_timeout_reported_on_next_call(dev):
     s.check()
     _assert_matches_oracle(w, s, f, out)
     # host output: the call checks the flag itself before returning
-    s.set_wait_limit(1)
+    s.set_wait_limit(2000, withhold_copies=True)
     with pytest.raises(FWHError) as ei:
         s.forward(f.cpu())
     assert ei.value.status == _abi.FWH_ERR_TIMEOUT
@@ -101,7 +102,7 @@ def test_timeout_reaches_autograd(dev):
     from paper_2312_16263_gb300 import fwh_apply
     from paper_2312_16263_gb300._abi import FWHError
     w, s, f = _case(dev, "mixed")
-    s.set_wait_limit(1)
+    s.set_wait_limit(2000, withhold_copies=True)
     p = fwh_apply(s, f.clone().requires_grad_(True))
     torch.cuda.synchronize()
     s.set_wait_limit(0)
