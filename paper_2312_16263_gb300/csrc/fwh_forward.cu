@@ -45,6 +45,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "fwh_internal.cuh"
 
@@ -570,15 +571,18 @@ __device__ __forceinline__ void consume_item(const FwdArgs<T> &a, const Item<T, 
 // __syncwarp per panel orders the next panel's shifted updates.
 // Shared-space accesses by 32-bit address (the consumer addresses the stage
 // ring and its windows explicitly, so no generic-address arithmetic).
-__device__ __forceinline__ float lds_f32(unsigned addr) {
+// Window loads are not volatile: the compiler may hoist an observer's loads
+// above the previous observer's stores (their windows never overlap), which
+// hides their latency.  They stay after the previous panel's stores because
+// their addresses derive from a token taken after that panel's __syncwarp.
+__device__ __forceinline__ float lds_win(unsigned addr) {
   float v;
-  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
   return v;
 }
 __device__ __forceinline__ void sts_f32(unsigned addr, float v) {
   asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
-
 // Loads of stage data (X rows, records): not volatile, so the compiler may
 // schedule them early; they stay after the stage's full-barrier wait because
 // their addresses derive from stage_token(), which that wait orders.
@@ -603,7 +607,7 @@ __device__ __forceinline__ unsigned stage_token(unsigned addr) {
 // x + (the value of the lane above, if there is one): the last lane keeps x.
 __device__ __forceinline__ float add_from_lane_above(float x, float v) {
   float r;
-  asm volatile(
+  asm(
       "{\n\t.reg .pred p;\n\t.reg .f32 t;\n\t"
       "shfl.sync.down.b32 t|p, %2, 1, 0x1f, 0xffffffff;\n\t"
       "mov.f32 %0, %1;\n\t"
@@ -729,22 +733,23 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
         }
       }
       const unsigned crec = stg + ps.x_bytes + (unsigned)w * RB;
-      // PF: read the next observer's record while this one computes, else
-      // read each record right before its use.
-      Coef k;
-      if (PF && it.nobs > 0) lds_coef(crec, k);
-#pragma unroll
-      for (int m = 0; m < kMaxObsPerWarpF32; ++m) {
-        if (m >= it.nobs) break;
-        if (!PF) lds_coef(crec + (unsigned)m * NW * RB, k);
-        const unsigned base = win_s + (unsigned)m * win_b;
+      // window base of this panel's updates, ordered after the previous
+      // panel's stores (see lds_win)
+      const unsigned wtok = stage_token(win_s);
+      // one (panel, observer): the spline-node updates of the lane's samples
+      auto observer = [&](int m, const Coef &k) {
+        const unsigned base = wtok + (unsigned)m * win_b;
         const unsigned A0 = base + k.r0, A1 = base + k.r1;
         float s0[NP], s1[NP], v0[NP];
 #pragma unroll
         for (int t = 0; t < NP; ++t) {
-          s0[t] = lds_f32(A0 + 128u * t);
-          s1[t] = lds_f32(A1 + 128u * t);
+          s0[t] = lds_win(A0 + 128u * t);
+          s1[t] = lds_win(A1 + 128u * t);
         }
+        // lane 0: the slot below the chunk (other lanes read a slot of the
+        // lane below, in the window, and discard it); no lane stores to it
+        // before lane 0 does, so it is read early to hide the latency
+        const float e_old = lds_win(A1 - 4u);
 #pragma unroll
         for (int t = 0; t < NP; ++t) {
           float G0 = k.c[0] * X[t][0][0], M0 = k.c[0] * X[t][0][8];
@@ -763,8 +768,13 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
           // right node of the pair's first sample, for the lane below
           v0[t] = fmaf(k.wdd, M0, k.wb * G0);
         }
-        Coef kn;
-        if (PF && m + 1 < it.nobs) lds_coef(crec + (unsigned)(m + 1) * NW * RB, kn);
+#pragma unroll
+        for (int t = 0; t < NP; ++t) sts_f32(A0 + 128u * t, s0[t]);
+        // Lane 0 stores the slot below the chunk.  Every other lane stores the
+        // same expression to its A1 - 4, which is the slot of the lane below's
+        // second sample in block 0: that lane's own store to it comes later in
+        // program order and overwrites it, so no predicate is needed.
+        sts_f32(A1 - 4u, e_old + v0[0]);
 #pragma unroll
         for (int t = 0; t + 1 < NP; ++t) {
           // lane 0 serves lane 31 with block t + 1's first sample
@@ -773,16 +783,32 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
         }
         s1[NP - 1] = add_from_lane_above(s1[NP - 1], v0[NP - 1]);
 #pragma unroll
-        for (int t = 0; t < NP; ++t) {
-          sts_f32(A0 + 128u * t, s0[t]);
-          sts_f32(A1 + 128u * t, s1[t]);
+        for (int t = 0; t < NP; ++t) sts_f32(A1 + 128u * t, s1[t]);
+      };
+      // PF: read the next observer's record while this one computes, else
+      // read each record right before its use.  A warp with the full count of
+      // observers runs them without an exit test, so the compiler may overlap
+      // one observer's tail with the next one's loads and arithmetic.
+      auto run = [&](auto full) {
+        constexpr bool kFull = decltype(full)::value;
+        const int n = kFull ? kMaxObsPerWarpF32 : it.nobs;
+        auto rec = [&](int m) { return crec + (unsigned)m * NW * RB; };
+        Coef k;
+        if (PF && n > 0) lds_coef(rec(0), k);
+#pragma unroll
+        for (int m = 0; m < kMaxObsPerWarpF32; ++m) {
+          if (!kFull && m >= n) break;
+          if (!PF) lds_coef(rec(m), k);
+          Coef kn;
+          if (PF && m + 1 < n) lds_coef(rec(m + 1), kn);
+          observer(m, k);
+          if (PF) k = kn;
         }
-        if (first) {  // the slot below the chunk: right node of sample 0
-          const unsigned ae = A1 - 4u;
-          sts_f32(ae, lds_f32(ae) + v0[0]);
-        }
-        if (PF && m + 1 < it.nobs) k = kn;
-      }
+      };
+      if (it.nobs == kMaxObsPerWarpF32)
+        run(std::true_type{});
+      else
+        run(std::false_type{});
       __syncwarp();
       if constexpr (PIPE == 2) {
         // the last warp done with this stage refills it with step j + nst
@@ -1034,12 +1060,16 @@ __global__ void __maxnreg__(200)
 // same with the next observer's record read ahead.  wide: register cap 200
 // instead of the launch bounds' occupancy target.
 constexpr FwdConfig kCfgF32[] = {
-    {1, 4, 4, 9, 224, 4, 3, 3, 0},
-    {1, 4, 4, 9, 224, 2, 3, 3, 0},
     {1, 4, 4, 9, 224, 4, 3, 4, 0},
-    {2, 4, 4, 9, 224, 4, 2, 3, 0},
-    {2, 4, 8, 9, 224, 4, 3, 3, 0},
+    {1, 4, 4, 9, 224, 2, 3, 4, 0},
+    {1, 4, 4, 9, 224, 4, 3, 3, 0},
+    {2, 4, 4, 9, 224, 4, 2, 4, 0},
+    {2, 4, 8, 9, 224, 4, 3, 4, 0},
     {1, 8, 4, 9, 352, 2, 3, 3, 0},
+    {1, 4, 4, 9, 224, 4, 3, 4, 1},
+    {1, 4, 4, 9, 224, 8, 3, 4, 0},
+    {1, 4, 4, 9, 160, 4, 4, 4, 0},
+    {1, 4, 4, 9, 224, 4, 2, 4, 0},
 };
 constexpr bool f32_obs_fit() {
   for (const FwdConfig &c : kCfgF32)
@@ -1139,13 +1169,14 @@ bool encode_x_tensor_map(void *out128, const void *X, unsigned long long rows, b
   return r == CUDA_SUCCESS;
 }
 
-// Instantiated shapes: FP32 {TMA packed 4x8, 4x4, 8x4}; FP64 {direct 2x8,
-// TMA 2x8, direct 2x4, direct 1x8}.
+// Instantiated shapes: FP32 {copy warp: TK 4 with and without the record read
+// ahead, TK 8; in-line refill: 4 and 8 warps}; FP64 {direct 2x8, TMA 2x8,
+// direct 2x4, direct 1x8}.
 #define FWH_DISPATCH(T, c, CALL)                                                        \
   do {                                                                                   \
     if constexpr (sizeof(T) == 4) {                                                      \
-      if (c.pipe == 2 && c.tk == 4 && c.warps == 4 && c.acc == 3) return CALL(T, 4, 4, 2, 3); \
-      if (c.pipe == 2 && c.tk == 4 && c.warps == 8 && c.acc == 3) return CALL(T, 4, 8, 2, 3); \
+      if (c.pipe == 2 && c.tk == 4 && c.warps == 4 && c.acc == 4) return CALL(T, 4, 4, 2, 4); \
+      if (c.pipe == 2 && c.tk == 4 && c.warps == 8 && c.acc == 4) return CALL(T, 4, 8, 2, 4); \
       if (c.pipe == 1 && c.tk == 4 && c.warps == 4 && c.acc == 3) return CALL(T, 4, 4, 1, 3); \
       if (c.pipe == 1 && c.tk == 4 && c.warps == 4 && c.acc == 4) return CALL(T, 4, 4, 1, 4); \
       if (c.pipe == 1 && c.tk == 8 && c.warps == 4 && c.acc == 3) return CALL(T, 8, 4, 1, 3); \
