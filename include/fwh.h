@@ -227,6 +227,31 @@ fwh_status fwh_forward_noalloc(fwh_handle h, const void *fields, int64_t nt, dou
                                void *stream);
 
 /*
+ * Power spectral density of far-field signals (Sec. IV C): Welch's method
+ * with segments of nperseg samples overlapping by 50 %, a periodic Hanning
+ * window w[n] = 0.5 - 0.5 cos(2 pi n / nperseg) on each segment (its mean
+ * removed first when detrend = 1), the squared magnitudes of the segments'
+ * discrete Fourier transforms averaged over the K = floor((N - nperseg) /
+ * (nperseg / 2)) + 1 segments of a signal's N valid samples, divided by
+ * fs * sum(w^2) and doubled at 0 < k < nperseg / 2 (one-sided density), then
+ * the span correction of Eq. PSD_corr: multiplied by span_ratio = b_exp / b_m,
+ * and with p_ref > 0 returned in dB, 10 log10(PSD span_ratio / p_ref^2).
+ * Arguments: p [n_sig][ld] doubles (host or device; row s holds signal s),
+ * n_valid [n_sig] int64 (host or device; N of each signal, in [0, ld]; NULL:
+ * every signal has ld samples -- for fwh_forward output pass the window of
+ * fwh_observer_window), fs > 0 the sampling rate (1/dt for the observer
+ * grid), nperseg a power of two in [16, 4096], psd [n_sig][nperseg/2 + 1]
+ * doubles (host or device) at frequencies k fs / nperseg.  A signal shorter
+ * than one segment gets NaN in every bin.  Computed in FP64, one CTA per
+ * signal, on `stream`; host buffers are staged and the call then
+ * synchronises.  Errors: FWH_ERR_ARG (sizes, ranges, null pointers),
+ * FWH_ERR_OOM / FWH_ERR_CUDA (message via fwh_last_error(NULL)).
+ */
+fwh_status fwh_psd(int64_t n_sig, const double *p, int64_t ld, const int64_t *n_valid,
+                   double fs, int64_t nperseg, int detrend, double span_ratio, double p_ref,
+                   double *psd, void *stream);
+
+/*
  * Measured fused multiply-add throughput of the current GPU (TFLOP/s, 2 flop
  * per FMA): FP32 for FWH_MIXED, FP64 for FWH_FP64, from independent FMA
  * chains on every SM timed with CUDA events on `stream` (about 60 ms; the

@@ -16,7 +16,7 @@ from .build import build  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("FWH", "batch_forward"):
+    if name in ("FWH", "batch_forward", "welch_psd"):
         from . import api
         return getattr(api, name)
     if name in ("fwh_apply", "FWHFunction"):
@@ -25,4 +25,4 @@ def __getattr__(name):
     raise AttributeError(name)
 
 
-__all__ = ["FWH", "batch_forward", "build", "fwh_apply", "FWHFunction"]
+__all__ = ["FWH", "batch_forward", "build", "fwh_apply", "FWHFunction", "welch_psd"]

@@ -153,6 +153,29 @@ class FWH:
         _abi.check(self.lib.fwh_check(self.h, _stream_ptr(stream)), self.h)
 
 
+def welch_psd(p: torch.Tensor, fs: float, nperseg: int, n_valid=None, detrend: bool = True,
+              span_ratio: float = 1.0, p_ref: float = 0.0, out: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+    """Span-corrected Welch PSD of each row of p [n_sig][ld] (fwh_psd; Sec. IV C,
+    Eq. PSD_corr).  n_valid: samples per row (e.g. FWH.window(nt)[1]) or None.
+    Returns [n_sig][nperseg // 2 + 1] float64 on p's device."""
+    if p.dtype != torch.float64 or p.dim() != 2 or not p.is_contiguous():
+        raise ValueError("p must be a contiguous [n_sig][ld] float64 tensor")
+    n_sig, ld = p.shape
+    if out is None:
+        out = torch.empty((n_sig, nperseg // 2 + 1), dtype=torch.float64, device=p.device)
+    nv = None
+    if n_valid is not None:
+        nv = torch.as_tensor(np.asarray(n_valid, dtype=np.int64) if not isinstance(
+            n_valid, torch.Tensor) else n_valid, dtype=torch.int64).contiguous()
+    lib = _abi.load()
+    _abi.check(lib.fwh_psd(n_sig, ctypes.c_void_p(p.data_ptr()), ld,
+                           ctypes.c_void_p(nv.data_ptr()) if nv is not None else None,
+                           float(fs), int(nperseg), int(bool(detrend)), float(span_ratio),
+                           float(p_ref), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
 def batch_forward(surfaces: Sequence[FWH], fields: Sequence[torch.Tensor],
                   outs: Sequence[torch.Tensor] | None = None, stream=None):
     """One persistent, graph-captured launch over several surfaces."""
