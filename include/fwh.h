@@ -100,6 +100,23 @@ fwh_status fwh_create(fwh_handle *out, int64_t n_panels, const double *centroids
 fwh_status fwh_set_observers(fwh_handle h, int64_t n_obs, const double *xyz);
 
 /*
+ * Panel sharding (the paper's Face partition, Sec. III A, with the
+ * MPI_ALLREDUCE of R_max / R_min of Sec. III B "compute t"): a handle made on
+ * one rank's subset of the subfaces reports, per observer, the largest and
+ * smallest convected distance R over its own panels (host arrays [O]); the
+ * ranks reduce them (maximum of r_max, minimum of r_min) and each sets the
+ * global values on its handle.  Every rank then has the same observer window
+ * (t_start = M0 R_max, Eq. t_start; N_o from Eq. t_end), its forward pass
+ * yields its panels' share of p_out on that common grid, and a sum over the
+ * ranks gives the unsharded result.  fwh_set_observer_extremes recomputes
+ * the shifts and spline weights of the records and the panel-set plan; it
+ * refuses (FWH_ERR_ARG) extremes that do not enclose the handle's own, and
+ * fwh_set_observers restores the handle's own extremes.
+ */
+fwh_status fwh_observer_extremes(fwh_handle h, double *r_max, double *r_min);
+fwh_status fwh_set_observer_extremes(fwh_handle h, const double *r_max, const double *r_min);
+
+/*
  * Forward pass: far-field pressure p_out [O][nt] (double) from the fields
  * [nt][5][P] (double for FWH_FP64, float for FWH_MIXED), nt >= 3.
  * Covers the "compute Noise", "compute t", "interp pressure signal" and

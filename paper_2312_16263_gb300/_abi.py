@@ -31,6 +31,8 @@ SIGNATURES = {
     "fwh_forward": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "fwh_forward_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "fwh_observer_window": (ctypes.c_int, [_vp, _i64, _dp, _ip64]),
+    "fwh_observer_extremes": (ctypes.c_int, [_vp, _dp, _dp]),
+    "fwh_set_observer_extremes": (ctypes.c_int, [_vp, _dp, _dp]),
     "fwh_backward": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "fwh_batch_forward": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_vp),
                                          ctypes.POINTER(_vp), _ip64, ctypes.POINTER(_vp),

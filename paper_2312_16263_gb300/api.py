@@ -83,6 +83,23 @@ class FWH:
             nv.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), self.h)
         return ts, nv
 
+    def observer_extremes(self):
+        """(R_max, R_min) per observer over this surface's own panels."""
+        mx = np.empty(self.O, dtype=np.float64)
+        mn = np.empty(self.O, dtype=np.float64)
+        _abi.check(self.lib.fwh_observer_extremes(
+            self.h, mx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            mn.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), self.h)
+        return mx, mn
+
+    def set_observer_extremes(self, r_max, r_min):
+        """Use the given (all-reduced) extremes for the observer window."""
+        mx = np.ascontiguousarray(r_max, dtype=np.float64)
+        mn = np.ascontiguousarray(r_min, dtype=np.float64)
+        _abi.check(self.lib.fwh_set_observer_extremes(
+            self.h, mx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            mn.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), self.h)
+
     def _check_fields(self, fields: torch.Tensor):
         if fields.dtype != self.dtype:
             raise TypeError(f"fields must be {self.dtype} for precision {self.precision}")

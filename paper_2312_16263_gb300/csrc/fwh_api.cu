@@ -56,7 +56,8 @@ struct fwh_ctx {
   std::vector<int> perm;          // library position -> caller index
   bool identity = true;
   std::vector<double> xobs;
-  std::vector<double> Rmax, Rmin;
+  std::vector<double> Rmax, Rmin;            // window extremes in use (local or set)
+  std::vector<double> Rmax_loc, Rmin_loc;    // over this handle's own panels
   // device state
   double *d_y = nullptr, *d_n = nullptr, *d_dS = nullptr, *d_x = nullptr;
   double *d_Rmax = nullptr, *d_Rmin = nullptr;
@@ -738,10 +739,64 @@ fwh_status fwh_set_observers(fwh_handle h, int64_t O, const double *xyz) {
   h->Rmin.resize(O);
   CK(h, cudaMemcpy(h->Rmax.data(), h->d_Rmax, O * sizeof(double), cudaMemcpyDeviceToHost));
   CK(h, cudaMemcpy(h->Rmin.data(), h->d_Rmin, O * sizeof(double), cudaMemcpyDeviceToHost));
+  h->Rmax_loc = h->Rmax;
+  h->Rmin_loc = h->Rmin;
   h->xobs = x;
   h->O = O;
   h->nt = -1;         // window depends on the observers
   h->plan_win = -1;   // records were rewritten: window offsets must be re-planned
+  drop_graphs(h);
+  return plan_default(h);
+}
+
+fwh_status fwh_observer_extremes(fwh_handle h, double *r_max, double *r_min) {
+  if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
+  if (h->O < 1) return fail(h, FWH_ERR_STATE, "observers not set");
+  for (int64_t o = 0; o < h->O; ++o) {
+    if (r_max) r_max[o] = h->Rmax_loc[o];
+    if (r_min) r_min[o] = h->Rmin_loc[o];
+  }
+  return FWH_OK;
+}
+
+fwh_status fwh_set_observer_extremes(fwh_handle h, const double *r_max, const double *r_min) {
+  if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
+  if (h->O < 1) return fail(h, FWH_ERR_STATE, "observers not set");
+  if (!r_max || !r_min) return fail(h, FWH_ERR_ARG, "r_max or r_min is NULL");
+  for (int64_t o = 0; o < h->O; ++o) {
+    if (!std::isfinite(r_max[o]) || !std::isfinite(r_min[o]))
+      return fail(h, FWH_ERR_ARG, "extremes must be finite");
+    if (r_max[o] < h->Rmax_loc[o] || r_min[o] > h->Rmin_loc[o])
+      return fail(h, FWH_ERR_ARG,
+                  "observer " + std::to_string(o) +
+                      ": the extremes must enclose this handle's own (r_max >= its largest R, "
+                      "r_min <= its smallest)");
+  }
+  std::vector<double> mx(r_max, r_max + h->O), mn(r_min, r_min + h->O);
+  CK(h, cudaMemcpy(h->d_Rmax, mx.data(), h->O * sizeof(double), cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(h->d_Rmin, mn.data(), h->O * sizeof(double), cudaMemcpyHostToDevice));
+  GeomArgs g{};
+  g.y = h->d_y;
+  g.n = h->d_n;
+  g.dS = h->d_dS;
+  g.x = h->d_x;
+  g.P = (int)h->P;
+  g.O = (int)h->O;
+  g.mach = h->mach;
+  g.ca = h->ca;
+  g.sa = h->sa;
+  g.dt = h->dt;
+  g.Rmax = h->d_Rmax;
+  g.Rmin = h->d_Rmin;
+  // records: shifts and spline weights relative to the new t_start (Eq. t_start)
+  if (h->precision == FWH_FP64)
+    CK(h, launch_coef<double>(g, reinterpret_cast<double *>(h->coef.p), 0));
+  else
+    CK(h, launch_coef<float>(g, reinterpret_cast<float *>(h->coef.p), 0));
+  h->Rmax = mx;
+  h->Rmin = mn;
+  h->nt = -1;
+  h->plan_win = -1;
   drop_graphs(h);
   return plan_default(h);
 }

@@ -583,6 +583,16 @@ __device__ __forceinline__ float lds_win(unsigned addr) {
 __device__ __forceinline__ void sts_f32(unsigned addr, float v) {
   asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
+// Store by the lanes whose `on` is set (the others store nothing).
+__device__ __forceinline__ void sts_f32_if(bool on, unsigned addr, float v) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %2, 0;\n\t"
+      "@p st.shared.f32 [%0], %1;\n\t}" ::"r"(addr),
+      "f"(v), "r"((unsigned)on)
+      : "memory");
+}
+
 // Loads of stage data (X rows, records): not volatile, so the compiler may
 // schedule them early; they stay after the stage's full-barrier wait because
 // their addresses derive from stage_token(), which that wait orders.
@@ -770,11 +780,6 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
         }
 #pragma unroll
         for (int t = 0; t < NP; ++t) sts_f32(A0 + 128u * t, s0[t]);
-        // Lane 0 stores the slot below the chunk.  Every other lane stores the
-        // same expression to its A1 - 4, which is the slot of the lane below's
-        // second sample in block 0: that lane's own store to it comes later in
-        // program order and overwrites it, so no predicate is needed.
-        sts_f32(A1 - 4u, e_old + v0[0]);
 #pragma unroll
         for (int t = 0; t + 1 < NP; ++t) {
           // lane 0 serves lane 31 with block t + 1's first sample
@@ -784,6 +789,7 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
         s1[NP - 1] = add_from_lane_above(s1[NP - 1], v0[NP - 1]);
 #pragma unroll
         for (int t = 0; t < NP; ++t) sts_f32(A1 + 128u * t, s1[t]);
+        sts_f32_if(first, A1 - 4u, e_old + v0[0]);  // lane 0: the slot below the chunk
       };
       // PF: read the next observer's record while this one computes, else
       // read each record right before its use.  A warp with the full count of
