@@ -154,15 +154,32 @@ fwh_status fwh_backward(fwh_handle h, const void *fields, int64_t nt,
 
 /*
  * Batched forward over n handles (several uneven surfaces, each with its own
- * observers, fields, nt and p_out), run by one persistent work-queue kernel
- * over the work items of every surface; all handles must share one precision.  With device
- * buffers the launch sequence is captured once in a CUDA graph keyed on the
- * handle set and replayed on later calls with the same arguments.
+ * observers, fields, nt and p_out); all handles must share one precision and
+ * take device buffers.  Source time is streamed in segments (512 samples
+ * under the default tile shape): per segment, the series of every surface are
+ * prepared on a high-priority stream, then one persistent work-queue kernel
+ * scatters the work items of every surface in that segment, while the next
+ * segment is being prepared.  A surface whose record spans more than two
+ * segments keeps only a ring of two segments of series (P x 1024 rows instead
+ * of P x round_up(nt, 256)).  The whole sequence is captured once in a CUDA
+ * graph keyed on the handle set and replayed on later calls with the same
+ * arguments.
  * Errors: FWH_ERR_ARG (n < 1, mixed precisions, null entries),
  * FWH_ERR_STATE (a handle without observers), FWH_ERR_CUDA.
  */
 fwh_status fwh_batch_forward(int n, const fwh_handle *hs, const void *const *fields,
                              const int64_t *nt, double *const *p_out, void *stream);
+
+/*
+ * Pipelined forward passes (default on): with device fields and a record of
+ * several time segments (512 samples under the default tile shape),
+ * fwh_forward prepares the series of each segment on a high-priority stream
+ * the handle owns and starts the scatter of a segment as soon as its series
+ * are in, so the preparation of later segments runs under the scatter of
+ * earlier ones; off, it prepares the whole record first and scatters it in
+ * one launch.  Results agree to the FP64 rounding of the output sums.
+ */
+fwh_status fwh_set_pipeline(fwh_handle h, int enable);
 
 /*
  * Autotune: time the candidate tile shapes of the forward kernel on this

@@ -40,6 +40,7 @@ SIGNATURES = {
     "fwh_autotune": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(ctypes.c_int), _vp]),
     "fwh_set_tile_config": (ctypes.c_int, [_vp, ctypes.c_int]),
     "fwh_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "fwh_set_pipeline": (ctypes.c_int, [_vp, ctypes.c_int]),
     "fwh_set_wait_limit": (ctypes.c_int, [_vp, _i64, ctypes.c_int]),
     "fwh_last_timings": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "fwh_timing_totals": (ctypes.c_int, [_vp, _dp, _ip64, ctypes.c_int]),

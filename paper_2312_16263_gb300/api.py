@@ -151,6 +151,10 @@ class FWH:
         _abi.check(self.lib.fwh_set_wait_limit(self.h, int(cycles), int(bool(withhold_copies))),
                    self.h)
 
+    def set_pipeline(self, enable: bool = True):
+        """Overlap the series prep of later time segments with the scatter."""
+        _abi.check(self.lib.fwh_set_pipeline(self.h, int(bool(enable))), self.h)
+
     def set_timing(self, enable: bool = True):
         _abi.check(self.lib.fwh_set_timing(self.h, int(bool(enable))), self.h)
 

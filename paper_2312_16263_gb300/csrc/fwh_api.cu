@@ -41,10 +41,18 @@ struct Graph {
 };
 
 // Device-side argument table of one batched launch (lives with its graph).
+// Device-side argument tables of one batched call (live with its graph): per
+// time segment q, the FwdArgs of every surface and the prefix sums of their
+// work items.
 struct BatchPlan {
-  Buf args, prefix, counter;
-  int total = 0, ctas = 0, cfg = 0;
+  Buf args, prefix, counter;   // [nq][n] FwdArgs, [nq][n + 1] ints, [nq] ints
+  Buf tmaps;                   // [n] X tensor maps (128 bytes each)
+  std::vector<int> total;      // work items of each segment's persistent launch
+  std::vector<int> x_ld;       // X rows per panel of each surface (ring or whole record)
+  std::vector<int> nseg;       // time segments of each surface
+  int nq = 0, ctas = 0, cfg = 0, seg = 0;
 };
+constexpr int kRingSegs = 2;   // time segments of X a batched call keeps per surface
 
 }  // namespace
 
@@ -62,16 +70,16 @@ struct fwh_ctx {
   double *d_y = nullptr, *d_n = nullptr, *d_dS = nullptr, *d_x = nullptr;
   double *d_Rmax = nullptr, *d_Rmin = nullptr;
   int *d_perm = nullptr, *d_err = nullptr;
-  Buf coef, X, G, nvalid, sets, sord, stage_in, stage_out, stage_grad, tmap, imax;
-  // X tensor map: host copy (passed to single launches as a kernel parameter)
-  // and, for the batched form, a device copy
+  Buf coef, X, G, nvalid, sets, sord, stage_in, stage_out, stage_grad, imax;
+  // X tensor map (passed to single launches as a kernel parameter; batched
+  // calls keep device copies in their plans)
   alignas(64) unsigned char tmap_host[128] = {};
   const void *tmap_X = nullptr;  // X buffer / rows / box the host descriptor describes
   int tmap_box = 0;
   long long tmap_rows = 0;
-  bool tmap_dev_ok = false;      // the device copy equals the host descriptor
   long long wait_limit = 0;      // bound of the forward pipeline waits (0: default)
   int withhold = 0;              // testing: the forward pipeline issues no copies
+  bool pipeline = true;          // device fields: prep of later segments overlaps the scatter
   // deferred device check: each call with device outputs copies the error flag
   // into pinned host memory; the next call (or fwh_check) reads it
   int *h_err = nullptr;
@@ -258,7 +266,7 @@ fwh_status plan(fwh_handle h, const FwdConfig &c, cudaStream_t s) {
 // forward chunk (32 x TK samples) and prep chunk.
 constexpr int64_t kMaxNt = (int64_t)1 << 28;
 
-fwh_status prepare_nt(fwh_handle h, int64_t nt) {
+fwh_status prepare_window(fwh_handle h, int64_t nt) {
   if (nt < 3 || nt > kMaxNt)
     return fail(h, FWH_ERR_ARG, "nt must be in [3, 2^28] (got " + std::to_string(nt) + ")");
   if (h->precision == FWH_MIXED && h->P * ((nt + 255) / 256 * 256) >= ((int64_t)1 << 32))
@@ -282,6 +290,13 @@ fwh_status prepare_nt(fwh_handle h, int64_t nt) {
     h->nt = nt;
     h->ntp = (int)ntp;
   }
+  return FWH_OK;
+}
+
+// Window and the whole-record series buffer X.
+fwh_status prepare_nt(fwh_handle h, int64_t nt) {
+  fwh_status st = prepare_window(h, nt);
+  if (st != FWH_OK) return st;
   const size_t ts = tsize(h->precision);
   CK(h, ensure(h->X, (size_t)h->P * h->ntp * kRec * ts));
   return FWH_OK;
@@ -313,8 +328,8 @@ fwh_status plan_default(fwh_handle h) {
 
 // TMA descriptor of the handle's X buffer, kept on the host (re-encoded when
 // the buffer, its row count or the box changes).
-fwh_status ensure_tmap(fwh_handle h, int box_rows) {
-  const long long rows = (long long)h->P * h->ntp;
+fwh_status ensure_tmap(fwh_handle h, int box_rows, int x_ld = 0) {
+  const long long rows = (long long)h->P * (x_ld > 0 ? x_ld : h->ntp);
   if (h->tmap_X == h->X.p && h->tmap_rows == rows && h->tmap_box == box_rows) return FWH_OK;
   if (!encode_x_tensor_map(h->tmap_host, h->X.p, (unsigned long long)rows,
                            h->precision == FWH_FP64, box_rows))
@@ -322,18 +337,26 @@ fwh_status ensure_tmap(fwh_handle h, int box_rows) {
   h->tmap_X = h->X.p;
   h->tmap_rows = rows;
   h->tmap_box = box_rows;
-  h->tmap_dev_ok = false;
   return FWH_OK;
 }
 
-// Device copy of the descriptor, for the batched form's argument table.
-fwh_status ensure_tmap_dev(fwh_handle h, int box_rows) {
-  fwh_status st = ensure_tmap(h, box_rows);
-  if (st != FWH_OK) return st;
-  if (h->tmap.p && h->tmap_dev_ok) return FWH_OK;
-  CK(h, ensure(h->tmap, 128));
-  CK(h, cudaMemcpy(h->tmap.p, h->tmap_host, 128, cudaMemcpyHostToDevice));
-  h->tmap_dev_ok = true;
+
+// The handle's high-priority stream for the series prep of pipelined calls.
+fwh_status ensure_pstream(fwh_handle h) {
+  if (h->pstream) return FWH_OK;
+  int least = 0, greatest = 0;
+  CK(h, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  CK(h, cudaStreamCreateWithPriority(&h->pstream, cudaStreamNonBlocking, greatest));
+  return FWH_OK;
+}
+
+// At least n ordering events (no timing) in the handle's pool.
+fwh_status ensure_events(fwh_handle h, int n) {
+  while ((int)h->slab_ev.size() < n) {
+    cudaEvent_t e;
+    CK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    h->slab_ev.push_back(e);
+  }
   return FWH_OK;
 }
 
@@ -381,10 +404,12 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
   pa.ca = h->ca;
   pa.sa = h->sa;
   pa.dt = h->dt;
+  pa.x_ld = h->ntp;
   FwdArgs<T> fa{};
   fa.tmX = nullptr;
   fa.wait_cycles = h->wait_limit;
   fa.withhold = h->withhold;
+  fa.x_ld = h->ntp;
   fa.X = pa.X;
   fa.coef = reinterpret_cast<const T *>(h->coef.p);
   fa.p_out = d_pout;
@@ -403,10 +428,37 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
   fa.seg_lo = 0;
   fa.seg_cnt = fa.n_segs;
   fa.win = c.win;
-  if (host_fields == nullptr) {
+  if (host_fields == nullptr && (!h->pipeline || fa.n_segs < 2)) {
     CK(h, launch_prep<T>(pa, s));
     if (tev) CK(h, cudaEventRecord(tev[1], s));
     CK(h, launch_forward<T>(fa, c.pipe ? h->tmap_host : nullptr, cfg, s));
+  } else if (host_fields == nullptr) {
+    // Device fields, several time segments: the series of segment q are
+    // prepared on the high-priority prep stream and the scatter of segment q
+    // starts as soon as they are in, so the preparation of the later segments
+    // runs under the scatter of the earlier ones.  The prep stream first waits
+    // for the work already on `s` (the previous call's scatter reads X).
+    fwh_status st1 = ensure_pstream(h);
+    if (st1 != FWH_OK) return st1;
+    st1 = ensure_events(h, fa.n_segs + 1);
+    if (st1 != FWH_OK) return st1;
+    cudaEvent_t *ev_x = h->slab_ev.data(), ev_go = ev_x[fa.n_segs];
+    CK(h, cudaEventRecord(ev_go, s));
+    CK(h, cudaStreamWaitEvent(h->pstream, ev_go, 0));
+    const int cps = fa.seg_len / 64;  // 64-sample prep chunks per segment
+    for (int q = 0; q < fa.n_segs; ++q) {
+      pa.c_lo = q * cps;
+      pa.c_hi = std::min(h->ntp / 64, (q + 1) * cps);
+      CK(h, launch_prep<T>(pa, h->pstream));
+      CK(h, cudaEventRecord(ev_x[q], h->pstream));
+    }
+    for (int q = 0; q < fa.n_segs; ++q) {
+      CK(h, cudaStreamWaitEvent(s, ev_x[q], 0));
+      if (tev && q == 0) CK(h, cudaEventRecord(tev[1], s));
+      fa.seg_lo = q;
+      fa.seg_cnt = 1;
+      CK(h, launch_forward<T>(fa, c.pipe ? h->tmap_host : nullptr, cfg, s));
+    }
   } else {
     // Three streams: `copy` moves the slabs, `prep` (high priority, so that
     // its blocks get onto SMs between the scatter's) prepares slab q - 1 once
@@ -418,18 +470,12 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
     const int nslab = (int)((h->nt + kSlab - 1) / kSlab);
     const size_t row = (size_t)5 * h->P * sizeof(T);
     if (!h->copy) CK(h, cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking));
-    if (!h->pstream) {
-      int least = 0, greatest = 0;
-      CK(h, cudaDeviceGetStreamPriorityRange(&least, &greatest));
-      CK(h, cudaStreamCreateWithPriority(&h->pstream, cudaStreamNonBlocking, greatest));
-    }
+    fwh_status st1 = ensure_pstream(h);
+    if (st1 != FWH_OK) return st1;
     fa.seg_len = 2 * 32 * c.tk;
     fa.n_segs = (h->ntp + fa.seg_len - 1) / fa.seg_len;
-    while ((int)h->slab_ev.size() < 2 * nslab + 1) {
-      cudaEvent_t e;
-      CK(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-      h->slab_ev.push_back(e);
-    }
+    st1 = ensure_events(h, 2 * nslab + 1);
+    if (st1 != FWH_OK) return st1;
     cudaEvent_t *ev_in = h->slab_ev.data(), *ev_x = ev_in + nslab, ev_go = ev_in[2 * nslab];
     CK(h, cudaEventRecord(ev_go, s));
     CK(h, cudaStreamWaitEvent(h->copy, ev_go, 0));
@@ -463,8 +509,8 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
       pa.c_hi = q < nslab ? q * cps : h->ntp / 64;
       CK(h, launch_prep<T>(pa, h->pstream));
       CK(h, cudaEventRecord(ev_x[j], h->pstream));
-      const fwh_status st1 = scatter_upto(pa.c_hi * 64, j);
-      if (st1 != FWH_OK) return st1;
+      const fwh_status st2 = scatter_upto(pa.c_hi * 64, j);
+      if (st2 != FWH_OK) return st2;
     }
   }
   if (tev) CK(h, cudaEventRecord(tev[2], s));
@@ -479,6 +525,7 @@ void drop_graphs(fwh_handle h) {
     release(kv.second.args);
     release(kv.second.prefix);
     release(kv.second.counter);
+    release(kv.second.tmaps);
   }
   h->bplans.clear();
 }
@@ -999,6 +1046,12 @@ fwh_status fwh_set_wait_limit(fwh_handle h, int64_t cycles, int withhold_copies)
   return FWH_OK;
 }
 
+fwh_status fwh_set_pipeline(fwh_handle h, int enable) {
+  if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
+  h->pipeline = enable != 0;
+  return FWH_OK;
+}
+
 fwh_status fwh_set_timing(fwh_handle h, int enable) {
   if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
   h->timing = enable != 0;
@@ -1042,6 +1095,7 @@ void fwh_destroy(fwh_handle h) {
     release(kv.second.args);
     release(kv.second.prefix);
     release(kv.second.counter);
+    release(kv.second.tmaps);
   }
   for (double *p : {h->d_y, h->d_n, h->d_dS, h->d_x, h->d_Rmax, h->d_Rmin})
     if (p) cudaFree(p);
@@ -1049,7 +1103,7 @@ void fwh_destroy(fwh_handle h) {
   if (h->d_err) cudaFree(h->d_err);
   for (Buf *b : {&h->coef, &h->X, &h->G, &h->nvalid, &h->sets, &h->sord, &h->stage_in,
                  &h->stage_out,
-                 &h->stage_grad, &h->tmap, &h->imax})
+                 &h->stage_grad, &h->imax})
     release(*b);
   for (int i = 0; i < 4; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
@@ -1076,32 +1130,56 @@ void fwh_destroy(fwh_handle h) {
 // ---------------------------------------------------------------------------
 namespace {
 
-template <typename T>
-fwh_status batch_build(int n, const fwh_handle *hs, const void *const *fields,
-                       double *const *p_out, fwh_handle h0, BatchPlan &bp) {
-  const bool fp64 = sizeof(T) == 8;
+// Tile configuration of a batched call (one for all surfaces).
+int batch_cfg(int n, const fwh_handle *hs, fwh_handle h0) {
+  const bool fp64 = h0->precision == FWH_FP64;
   int cfg = h0->cfg >= 0 ? h0->cfg : default_cfg(h0);
   for (int i = 0; i < n; ++i) {
     const int ci = effective_cfg(hs[i], hs[i]->ntp);
     if (fwd_config(fp64, ci).pipe != fwd_config(fp64, cfg).pipe) cfg = ci;
   }
+  return cfg;
+}
+
+// X rows per panel of a surface in a batched call: records longer than
+// kRingSegs time segments stream through a ring of kRingSegs segments.
+int batch_x_ld(const fwh_ctx *h, int seg) {
+  return (h->ntp + seg - 1) / seg > kRingSegs ? kRingSegs * seg : h->ntp;
+}
+
+template <typename T>
+fwh_status batch_build(int n, const fwh_handle *hs, double *const *p_out, fwh_handle h0,
+                       BatchPlan &bp) {
+  const bool fp64 = sizeof(T) == 8;
+  const int cfg = batch_cfg(n, hs, h0);
   const FwdConfig c = fwd_config(fp64, cfg);
-  std::vector<FwdArgs<T>> args(n);
-  std::vector<int> prefix(n + 1, 0);
+  const int seg = c.seg_chunks * 32 * c.tk;
+  std::vector<FwdArgs<T>> base(n);
+  std::vector<unsigned char> maps((size_t)n * 128, 0);
+  bp.x_ld.assign(n, 0);
+  bp.nseg.assign(n, 0);
+  bp.nq = 0;
+  CK(h0, ensure(bp.tmaps, (size_t)n * 128));
   for (int i = 0; i < n; ++i) {
     fwh_handle h = hs[i];
     fwh_status st = plan(h, c, h0->side);
     if (st != FWH_OK) return fail(h0, st, h->err);
     CK(h0, cudaStreamSynchronize(h0->side));
-    if (c.pipe != 0) {
-      st = ensure_tmap_dev(h, 32 * c.tk);
-      if (st != FWH_OK) return fail(h0, st, h->err);
-    }
-    FwdArgs<T> &fa = args[i];
-    fa.tmX = h->tmap.p;
+    bp.nseg[i] = (h->ntp + seg - 1) / seg;
+    bp.x_ld[i] = batch_x_ld(h, seg);
+    bp.nq = std::max(bp.nq, bp.nseg[i]);
+    if (h->X.bytes < (size_t)h->P * bp.x_ld[i] * kRec * sizeof(T))
+      return fail(h0, FWH_ERR_STATE, "series buffer of a batched surface is too small");
+    if (c.pipe != 0 &&
+        !encode_x_tensor_map(maps.data() + (size_t)i * 128, h->X.p,
+                             (unsigned long long)h->P * bp.x_ld[i], fp64, 32 * c.tk))
+      return fail(h0, FWH_ERR_CUDA, "cuTensorMapEncodeTiled refused the series layout");
+    FwdArgs<T> &fa = base[i];
+    fa.tmX = static_cast<unsigned char *>(bp.tmaps.p) + (size_t)i * 128;
     fa.wait_cycles = h0->wait_limit;
     fa.withhold = h0->withhold;
     fa.X = reinterpret_cast<const T *>(h->X.p);
+    fa.x_ld = bp.x_ld[i];
     fa.coef = reinterpret_cast<const T *>(h->coef.p);
     fa.p_out = p_out[i];
     fa.n_valid = reinterpret_cast<const int *>(h->nvalid.p);
@@ -1114,55 +1192,97 @@ fwh_status batch_build(int n, const fwh_handle *hs, const void *const *fields,
     fa.ntp = h->ntp;
     fa.nt = (int)h->nt;
     obs_tiling(h, c, &fa.obs_per_cta, &fa.n_obs_groups);
-    fa.seg_len = c.seg_chunks * 32 * c.tk;
-    fa.n_segs = (h->ntp + fa.seg_len - 1) / fa.seg_len;
-    fa.seg_lo = 0;
-    fa.seg_cnt = fa.n_segs;
+    fa.seg_len = seg;
+    fa.n_segs = bp.nseg[i];
     fa.win = c.win;
-    prefix[i + 1] = prefix[i] + fa.nsets * fa.n_obs_groups * fa.n_segs;
   }
-  (void)fields;
-  bp.total = prefix[n];
+  // one persistent launch per time segment over every surface's items of it
+  std::vector<FwdArgs<T>> args((size_t)bp.nq * n);
+  std::vector<int> prefix((size_t)bp.nq * (n + 1), 0);
+  bp.total.assign(bp.nq, 0);
+  for (int q = 0; q < bp.nq; ++q) {
+    for (int i = 0; i < n; ++i) {
+      FwdArgs<T> fa = base[i];
+      const bool has = q < bp.nseg[i];
+      fa.seg_lo = has ? q : 0;
+      fa.seg_cnt = 1;
+      args[(size_t)q * n + i] = fa;
+      prefix[(size_t)q * (n + 1) + i + 1] =
+          prefix[(size_t)q * (n + 1) + i] + (has ? fa.nsets * fa.n_obs_groups : 0);
+    }
+    bp.total[q] = prefix[(size_t)q * (n + 1) + n];
+  }
+  bp.seg = seg;
   bp.cfg = cfg;
-  CK(h0, ensure(bp.args, n * sizeof(FwdArgs<T>)));
-  CK(h0, ensure(bp.prefix, (n + 1) * sizeof(int)));
-  CK(h0, ensure(bp.counter, sizeof(int)));
-  CK(h0, cudaMemcpy(bp.args.p, args.data(), n * sizeof(FwdArgs<T>), cudaMemcpyHostToDevice));
-  CK(h0, cudaMemcpy(bp.prefix.p, prefix.data(), (n + 1) * sizeof(int),
+  CK(h0, cudaMemcpy(bp.tmaps.p, maps.data(), maps.size(), cudaMemcpyHostToDevice));
+  CK(h0, ensure(bp.args, args.size() * sizeof(FwdArgs<T>)));
+  CK(h0, ensure(bp.prefix, prefix.size() * sizeof(int)));
+  CK(h0, ensure(bp.counter, (size_t)bp.nq * sizeof(int)));
+  CK(h0, cudaMemcpy(bp.args.p, args.data(), args.size() * sizeof(FwdArgs<T>),
+                    cudaMemcpyHostToDevice));
+  CK(h0, cudaMemcpy(bp.prefix.p, prefix.data(), prefix.size() * sizeof(int),
                     cudaMemcpyHostToDevice));
   int dev = 0, sms = 0;
   CK(h0, cudaGetDevice(&dev));
   CK(h0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   int per_sm = 0;
   CK(h0, forward_batch_occupancy<T>(cfg, &per_sm));
-  bp.ctas = std::max(1, std::min(bp.total, sms * std::max(1, per_sm)));
+  bp.ctas = sms * std::max(1, per_sm);
   return FWH_OK;
 }
+
+// The batched call's device work, enqueued on `s` (captured into a graph):
+// per time segment q, the series prep of every surface on the prep stream
+// (high priority), then one persistent scatter over all surfaces' items of
+// segment q on `s`.  The prep of segment q + 1 runs under the scatter of q;
+// with a ring, the prep of q waits for the scatter of q - kRingSegs, whose
+// rows it overwrites.
+constexpr int kBatchEv = 64;  // ordering events reused cyclically
 
 template <typename T>
 fwh_status batch_enqueue(int n, const fwh_handle *hs, const void *const *fields,
                          double *const *p_out, fwh_handle h0, const BatchPlan &bp,
                          cudaStream_t s) {
-  for (int i = 0; i < n; ++i) {
-    fwh_handle h = hs[i];
-    CK(h0, cudaMemsetAsync(p_out[i], 0, (size_t)h->O * h->nt * sizeof(double), s));
-    PrepArgs<T> pa{};
-    pa.fields = reinterpret_cast<const T *>(fields[i]);
-    pa.perm = h->identity ? nullptr : h->d_perm;
-    pa.n = h->d_n;
-    pa.X = reinterpret_cast<T *>(h->X.p);
-    pa.P = (int)h->P;
-    pa.nt = (int)h->nt;
-    pa.ntp = h->ntp;
-    pa.ca = h->ca;
-    pa.sa = h->sa;
-    pa.dt = h->dt;
-    CK(h0, launch_prep<T>(pa, s));
+  for (int i = 0; i < n; ++i)
+    CK(h0, cudaMemsetAsync(p_out[i], 0, (size_t)hs[i]->O * hs[i]->nt * sizeof(double), s));
+  CK(h0, cudaMemsetAsync(bp.counter.p, 0, (size_t)bp.nq * sizeof(int), s));
+  cudaEvent_t *ev = h0->slab_ev.data();  // [0]: fork, [1]: join, then prep and scatter rings
+  cudaEvent_t *ev_prep = ev + 2, *ev_scat = ev + 2 + kBatchEv;
+  CK(h0, cudaEventRecord(ev[0], s));
+  CK(h0, cudaStreamWaitEvent(h0->pstream, ev[0], 0));
+  const int cps = bp.seg / 64;
+  for (int q = 0; q < bp.nq; ++q) {
+    if (q >= kRingSegs) CK(h0, cudaStreamWaitEvent(h0->pstream, ev_scat[(q - kRingSegs) % kBatchEv], 0));
+    for (int i = 0; i < n; ++i) {
+      if (q >= bp.nseg[i]) continue;
+      fwh_handle h = hs[i];
+      PrepArgs<T> pa{};
+      pa.fields = reinterpret_cast<const T *>(fields[i]);
+      pa.perm = h->identity ? nullptr : h->d_perm;
+      pa.n = h->d_n;
+      pa.X = reinterpret_cast<T *>(h->X.p);
+      pa.P = (int)h->P;
+      pa.nt = (int)h->nt;
+      pa.ntp = h->ntp;
+      pa.x_ld = bp.x_ld[i];
+      pa.ca = h->ca;
+      pa.sa = h->sa;
+      pa.dt = h->dt;
+      pa.c_lo = q * cps;
+      pa.c_hi = std::min(h->ntp / 64, (q + 1) * cps);
+      CK(h0, launch_prep<T>(pa, h0->pstream));
+    }
+    CK(h0, cudaEventRecord(ev_prep[q % kBatchEv], h0->pstream));
+    CK(h0, cudaStreamWaitEvent(s, ev_prep[q % kBatchEv], 0));
+    if (bp.total[q] > 0)
+      CK(h0, launch_forward_batch<T>(reinterpret_cast<const FwdArgs<T> *>(bp.args.p) + (size_t)q * n,
+                                     reinterpret_cast<const int *>(bp.prefix.p) + (size_t)q * (n + 1),
+                                     n, bp.total[q], reinterpret_cast<int *>(bp.counter.p) + q,
+                                     bp.cfg, std::min(bp.ctas, bp.total[q]), s));
+    CK(h0, cudaEventRecord(ev_scat[q % kBatchEv], s));
   }
-  CK(h0, cudaMemsetAsync(bp.counter.p, 0, sizeof(int), s));
-  CK(h0, launch_forward_batch<T>(reinterpret_cast<const FwdArgs<T> *>(bp.args.p),
-                                 reinterpret_cast<const int *>(bp.prefix.p), n, bp.total,
-                                 reinterpret_cast<int *>(bp.counter.p), bp.cfg, bp.ctas, s));
+  CK(h0, cudaEventRecord(ev[1], h0->pstream));
+  CK(h0, cudaStreamWaitEvent(s, ev[1], 0));
   return FWH_OK;
 }
 
@@ -1187,8 +1307,15 @@ extern "C" fwh_status fwh_batch_forward(int n, const fwh_handle *hs, const void 
     if (h->O < 1) return fail(h0, FWH_ERR_STATE, "a handle has no observers");
     if (!is_device_ptr(fields[i]) || !is_device_ptr(p_out[i]))
       return fail(h0, FWH_ERR_ARG, "batched forward takes device buffers");
-    fwh_status st = prepare_nt(h, nt[i]);
+    fwh_status st = prepare_window(h, nt[i]);
     if (st != FWH_OK) return fail(h0, st, h->err);
+  }
+  {  // series buffers (a ring of time segments for long records) before the key
+    const FwdConfig c = fwd_config(h0->precision == FWH_FP64, batch_cfg(n, hs, h0));
+    const int seg = c.seg_chunks * 32 * c.tk;
+    for (int i = 0; i < n; ++i)
+      CK(h0, ensure(hs[i]->X, (size_t)hs[i]->P * batch_x_ld(hs[i], seg) * kRec *
+                                  tsize(h0->precision)));
   }
   std::vector<uintptr_t> key;
   for (int i = 0; i < n; ++i) {
@@ -1211,11 +1338,16 @@ extern "C" fwh_status fwh_batch_forward(int n, const fwh_handle *hs, const void 
     CK(h0, cudaEventCreateWithFlags(&h0->bev[0], cudaEventDisableTiming));
     CK(h0, cudaEventCreateWithFlags(&h0->bev[1], cudaEventDisableTiming));
   }
+  {
+    fwh_status st0 = ensure_pstream(h0);
+    if (st0 == FWH_OK) st0 = ensure_events(h0, 2 + 2 * kBatchEv);
+    if (st0 != FWH_OK) return st0;
+  }
   auto it = h0->graphs.find(key);
   if (it == h0->graphs.end()) {
     BatchPlan &bp = h0->bplans[key];
-    fwh_status st = h0->precision == FWH_FP64 ? batch_build<double>(n, hs, fields, p_out, h0, bp)
-                                              : batch_build<float>(n, hs, fields, p_out, h0, bp);
+    fwh_status st = h0->precision == FWH_FP64 ? batch_build<double>(n, hs, p_out, h0, bp)
+                                              : batch_build<float>(n, hs, p_out, h0, bp);
     if (st != FWH_OK) return st;
     // capture on the side stream (the caller's may be the legacy stream)
     cudaGraph_t g = nullptr;
@@ -1295,6 +1427,7 @@ fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, d
   pa.P = (int)h->P;
   pa.nt = (int)nt;
   pa.ntp = ntp;
+  pa.x_ld = ntp;
   pa.ca = h->ca;
   pa.sa = h->sa;
   pa.dt = h->dt;
@@ -1303,6 +1436,7 @@ fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, d
   fa.tmX = nullptr;
   fa.wait_cycles = h->wait_limit;
   fa.withhold = h->withhold;
+  fa.x_ld = ntp;
   fa.X = d_X;
   fa.coef = reinterpret_cast<const T *>(h->coef.p);
   fa.p_out = d_pout;

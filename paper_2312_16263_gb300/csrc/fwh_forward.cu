@@ -398,7 +398,7 @@ __device__ __forceinline__ void process_item_direct(const FwdArgs<T> &a, int ite
   for (int k0 = it.k_begin; k0 < it.k_end; k0 += CH) {
     for (int p = it.p_begin; p < it.p_end; ++p) {
       T x[TK][kRec];
-      const T *Xp = a.X + ((size_t)p * a.ntp + k0 + lane) * kRec;
+      const T *Xp = a.X + ((size_t)p * a.x_ld + k0 % a.x_ld + lane) * kRec;
 #pragma unroll
       for (int j = 0; j < TK; ++j) load16<T>(Xp + (size_t)j * 32 * kRec, x[j]);
       const T *rec0 = a.coef + (size_t)p * a.O * kRec;
@@ -445,7 +445,7 @@ __device__ __forceinline__ void issue_step(const FwdArgs<T> &a, const Item<T, NW
   uint64_t *bar = &ps.full[slot];
   unsigned char *dst = ps.stage0 + (size_t)slot * ps.stage_bytes;
   mbar_expect_tx(bar, ps.x_bytes + cbytes);
-  const int row = p * a.ntp + k0;  // tensor rows are 128 bytes
+  const int row = p * a.x_ld + k0 % a.x_ld;  // tensor rows are 128 bytes
   tma_load_2d(dst, ps.tmap, 0, sizeof(T) == 4 ? row >> 1 : row, bar);
   bulk_load(dst + ps.x_bytes, a.coef + ((size_t)p * a.O + it.o_begin) * kRec, cbytes, bar);
 }
@@ -467,7 +467,7 @@ __device__ __forceinline__ void produce_item(const FwdArgs<T> &a, const Item<T, 
   // incrementally: this lane's per-step work stays short, since it is on the
   // critical path of every stage refill.
   auto src_x = [&](int pp, int kc) {
-    return a.X + ((size_t)(it.p_begin + pp) * a.ntp + it.k_begin + kc * CH) * kRec;
+    return a.X + ((size_t)(it.p_begin + pp) * a.x_ld + it.k_begin % a.x_ld + kc * CH) * kRec;
   };
   auto src_c = [&](int pp) {
     return a.coef + ((size_t)(it.p_begin + pp) * a.O + it.o_begin) * kRec;
@@ -495,7 +495,7 @@ __device__ __forceinline__ void produce_item(const FwdArgs<T> &a, const Item<T, 
     unsigned char *dst = ps.stage0 + (size_t)s * ps.stage_bytes;
     mbar_expect_tx(&ps.full[s], ps.x_bytes + cbytes);
     // tensor rows are 128 bytes: two FP32 samples or one FP64 sample
-    const int row = (it.p_begin + cp) * a.ntp + it.k_begin + ck * CH;
+    const int row = (it.p_begin + cp) * a.x_ld + it.k_begin % a.x_ld + ck * CH;
     tma_load_2d(dst, ps.tmap, 0, sizeof(T) == 4 ? row >> 1 : row, &ps.full[s]);
     bulk_load(dst + ps.x_bytes, src_c(cp), cbytes, &ps.full[s]);
     if (++cp == np) {

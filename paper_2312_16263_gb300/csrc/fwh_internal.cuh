@@ -70,10 +70,11 @@ struct PrepArgs {
   const T *fields;      // [nt][5][P] original order
   const int *perm;      // [P] sorted position -> original panel index
   const double *n;      // [P][3] sorted normals
-  T *X;                 // [P][ntp][16]
+  T *X;                 // [P][x_ld][16]: sample k of panel p in row p x_ld + k mod x_ld
   int P, nt, ntp, chunk;
+  int x_ld;             // X rows per panel: ntp, or a ring of whole time segments
   double ca, sa, dt;
-  int c_lo, c_hi;       // FP32: 64-sample chunks [c_lo, c_hi) to prepare (0, 0: all)
+  int c_lo, c_hi;       // 64-sample chunks [c_lo, c_hi) to prepare (0, 0: all)
   int int_lo, int_hi;   // FP32, set by the launcher: the interior chunks within [c_lo, c_hi)
 };
 
@@ -81,7 +82,7 @@ template <typename T>
 struct FwdArgs {
   const void *tmX;      // batched form: device CUtensorMap over X as [P*ntp rows][16]
                         // (single launches take the descriptor as a kernel parameter)
-  const T *X;           // [P][ntp][16]
+  const T *X;           // [P][x_ld][16] (sample k in row p x_ld + k mod x_ld)
   const T *coef;        // [P][O][16]
   double *p_out;        // [O][nt]
   const int *n_valid;   // [O]
@@ -90,6 +91,7 @@ struct FwdArgs {
   const int *i0max_tab; // [nsets][O] largest shift of each (panel set, observer)
   int *err;
   int nsets, O, ntp, nt;
+  int x_ld;             // X rows per panel (ntp, or a ring of whole time segments)
   int obs_per_cta, n_obs_groups;
   int seg_len, n_segs;
   int seg_lo, seg_cnt;  // this launch covers time segments [seg_lo, seg_lo + seg_cnt)

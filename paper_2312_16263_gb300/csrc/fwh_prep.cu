@@ -118,15 +118,17 @@ __global__ void __launch_bounds__(PrepTile<T>::panels * 8) k_prep(PrepArgs<T> a)
   const int tid = threadIdx.x;
   const int n_pt = (a.P + NP - 1) / NP;  // 1D grid: panel tile fastest, then chunk
   const int p0 = (int)(blockIdx.x % n_pt) * NP;
-  const int c0 = (int)(blockIdx.x / n_pt) * a.chunk;
+  const int c0 = (a.c_lo + (int)(blockIdx.x / n_pt)) * a.chunk;
   const int c1 = min(c0 + a.chunk, a.ntp);
   const int nt = a.nt;
+  // rows of this chunk sit at c0 mod x_ld in each panel's block of X
+  const long xoff = (long)(c0 % a.x_ld) - c0;
 
   if (c0 >= nt) {  // chunk past the record: zero rows
     for (int idx = tid; idx < NP * (c1 - c0) * kRec; idx += NT) {
       const int pl = idx / ((c1 - c0) * kRec);
       const int r = idx % ((c1 - c0) * kRec);
-      if (p0 + pl < a.P) a.X[((size_t)(p0 + pl) * a.ntp + c0) * kRec + r] = T(0);
+      if (p0 + pl < a.P) a.X[((size_t)(p0 + pl) * a.x_ld + c0 % a.x_ld) * kRec + r] = T(0);
     }
     return;
   }
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(PrepTile<T>::panels * 8) k_prep(PrepArgs<T> a)
   const int pl = tid >> 3;
   const int p = p0 + pl;
   if (p >= a.P) return;
-  T *Xp = a.X + (size_t)p * a.ntp * kRec;
+  T *Xp = a.X + ((long)p * a.x_ld + xoff) * kRec;  // row i of the chunk at Xp + i kRec
   for (int i = max(c0, nt); i < c1; ++i) {  // rows past the record
     Xp[xidx<T>(i, s)] = T(0);
     Xp[xidx<T>(i, 8 + s)] = T(0);
@@ -415,7 +417,7 @@ __global__ void __launch_bounds__(kIntThreads, 4) k_prep_iir_int(PrepArgs<float>
       const bool more = b + 1 < b1;
       if (more) issue(c0 + C + H + 1, C);  // rows of the next window, in flight meanwhile
       // ---- phase B: filters of block b ----------------------------------------
-      float *xr = a.X + ((size_t)(live_b ? pb : 0) * a.ntp + c0) * kRec;
+      float *xr = a.X + ((size_t)(live_b ? pb : 0) * a.x_ld + c0 % a.x_ld) * kRec;
       // one half row (slots q0 .. q0 + 7 of row r) from the four lanes of a
       // panel: lane qi stores slots q0 + 2 qi, q0 + 2 qi + 1 as one float4 after
       // taking its neighbours' pairs (slot order: d0 v0 d1 d2 | d3 v1 v2 v3)
@@ -498,7 +500,7 @@ __global__ void __launch_bounds__(kIirThreads, 6) k_prep_iir(PrepArgs<float> a) 
   const bool live_b = pb < a.P;
   // X rows of the tile: row r holds the sample pair c0 + 2 r, c0 + 2 r + 1;
   // this thread's samples c0 + 32 h + t fill rows 16 h + t / 2
-  float *xr = a.X + ((size_t)(live_b ? pb : 0) * a.ntp + c0 + 32 * h) * kRec;
+  float *xr = a.X + ((size_t)(live_b ? pb : 0) * a.x_ld + c0 % a.x_ld + 32 * h) * kRec;
   // slot q of the pair (t0, t0 + 1) (t0 even) as one float2
   auto put2 = [&](int t0, int q, float v0, float v1) {
     if (live_b) *reinterpret_cast<float2 *>(xr + (t0 >> 1) * 2 * kRec + q * 2) = make_float2(v0, v1);
@@ -1005,6 +1007,13 @@ cudaError_t launch_prep(const PrepArgs<T> &a0, cudaStream_t s) {
     constexpr int H = Prec<T>::halo;
     PrepArgs<T> a = a0;
     a.chunk = PrepTile<T>::chunk;
+    static_assert(PrepTile<T>::chunk == kIirChunk, "chunk ranges count 64-sample chunks");
+    if (a.c_hi == 0) {
+      a.c_lo = 0;
+      a.c_hi = (a.ntp + a.chunk - 1) / a.chunk;
+    }
+    if (a.c_lo < 0 || a.c_hi > (a.ntp + a.chunk - 1) / a.chunk || a.c_lo >= a.c_hi)
+      return cudaErrorInvalidValue;
     // integrand rows (chunk + 2 halos + 2 FD neighbours) x 4 x NP, plus the
     // right-halo elimination values H x (NP * 8)
     const size_t smem =
@@ -1012,7 +1021,7 @@ cudaError_t launch_prep(const PrepArgs<T> &a0, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_prep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    const long blocks = (long)((a.P + NP - 1) / NP) * ((a.ntp + a.chunk - 1) / a.chunk);
+    const long blocks = (long)((a.P + NP - 1) / NP) * (a.c_hi - a.c_lo);
     if (blocks <= 0) return cudaSuccess;
     if (blocks > INT32_MAX) return cudaErrorInvalidValue;
     k_prep<T><<<(unsigned)blocks, NP * 8, smem, s>>>(a);

@@ -9,6 +9,8 @@
 * the eight uneven surfaces of the batched form, scaled down, through one
   persistent launch, against the oracle and against one call per surface.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -89,6 +91,45 @@ def test_adjoint_against_fp64_finite_differences(dev, prec):
     assert np.abs(ga - fd).max() <= 1e-5 * scale, (np.abs(ga - fd).max(), scale)
     s.close()
     s64.close()
+
+
+def _host_bytes_free():
+    try:
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_AVPHYS_PAGES")
+    except (ValueError, OSError):
+        return 0
+
+
+@pytest.mark.parametrize("prec", ["mixed"])
+def test_batched_eight_surfaces_full_size(dev, prec):
+    """The eight uneven surfaces at full size (524288 panels, 4096 steps, 1024
+    observers each): one graph of per-segment persistent launches streaming
+    the series through a two-segment ring, checked against the oracle on two
+    observers of every surface (rel-L2 per observer at the mixed bar) and
+    against one fwh_forward call per surface."""
+    from paper_2312_16263_gb300 import FWH, batch_forward
+    ws = batch_workloads()
+    assert sum(w.surface.n_panels for w in ws) == 524288
+    surfs = [FWH.from_workload(w, prec) for w in ws]
+    fields = [w.fields(device=dev, dtype="float32") for w in ws]
+    outs = batch_forward(surfs, fields)
+    outs = batch_forward(surfs, fields)      # the replayed graph
+    surfs[0].check()
+    free = _host_bytes_free()
+    for w, s, f, p in zip(ws, surfs, fields, outs):
+        _, nv = s.window(w.nt)
+        pick = np.array([0, w.observers.shape[0] // 2])
+        # host FP64 fields and the oracle's integrand array: 72 bytes per panel-step
+        need = 72 * w.surface.n_panels * w.nt
+        if free and need > 0.5 * free:
+            pytest.skip(f"host memory: the oracle on {w.name} needs {need / 1e9:.0f} GB")
+        orc = Oracle.from_workload(w)
+        p_ref, _, nv_ref = orc.forward(f.double().cpu().numpy(), w.observers[pick])
+        assert _rel_l2(p.cpu().numpy(), nv, p_ref, nv_ref, pick) <= TOL[prec], w.name
+        single = s.forward(f)
+        torch.testing.assert_close(p, single, rtol=1e-12, atol=1e-12 * single.abs().max().item())
+        s.close()   # frees the whole-record series before the next surface's call
+    del outs
 
 
 def test_batched_uneven_surfaces(dev):

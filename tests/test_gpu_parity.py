@@ -279,6 +279,28 @@ def test_every_tile_config_agrees(dev, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("nt", [1024, 1100, 513])
+def test_segment_pipeline_matches_one_launch(dev, prec, nt):
+    """Device fields over several 512-sample segments: the pipelined call
+    (series of each segment prepared on the prep stream, the segment scattered
+    as soon as they are in) equals the prep-then-one-launch call to the FP64
+    rounding of the output sums (the same FP32 partial sums reach the output
+    bins, in another order)."""
+    from paper_2312_16263_gb300 import FWH
+    w = workload(4)
+    s = FWH.from_workload(w, prec)
+    f = w.fields(device=dev, dtype="float64" if prec == "fp64" else "float32", nt=nt)
+    s.set_pipeline(False)
+    ref = s.forward(f).clone()
+    s.set_pipeline(True)
+    for _ in range(2):
+        p = s.forward(f)
+        s.check()
+        torch.testing.assert_close(p, ref, rtol=1e-12, atol=1e-13 * ref.abs().max().item())
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_empty_observer_window_gives_zeros(dev, prec):
     """A record shorter than the arrival-time spread over the surface leaves no
     valid observer bin (N_o = 0): the output is all zeros, like the oracle's."""
