@@ -112,8 +112,10 @@ def batch_workloads(scale: float = 1.0, nt: int = 4096, n_obs: int = 1024):
     for i, P in enumerate(BATCH_PANELS):
         Ps = max(64, int(round(P * scale)))
         if i % 2 == 0:
-            n_pol = max(4, int(round(np.sqrt(Ps / 2))))
-            n_az = max(8, Ps // n_pol)
+            # a polar x azimuth grid of exactly Ps panels, azimuth about twice polar
+            divs = [d for d in range(4, Ps // 8 + 1) if Ps % d == 0]
+            n_pol = min(divs, key=lambda d: (abs(d - np.sqrt(Ps / 2)), d))
+            n_az = Ps // n_pol
             surf = uv_sphere(1.0 + 0.25 * i, n_pol, n_az, center=(3.0 * i, 0.0, 0.0))
             mach, aoa, dt = 0.5, 10 * DEG, 0.01
         else:

@@ -171,13 +171,17 @@ fwh_status fwh_batch_forward(int n, const fwh_handle *hs, const void *const *fie
                              const int64_t *nt, double *const *p_out, void *stream);
 
 /*
- * Pipelined forward passes (default on): with device fields and a record of
+ * Pipelined forward passes (default off): with device fields and a record of
  * several time segments (512 samples under the default tile shape),
  * fwh_forward prepares the series of each segment on a high-priority stream
  * the handle owns and starts the scatter of a segment as soon as its series
  * are in, so the preparation of later segments runs under the scatter of
  * earlier ones; off, it prepares the whole record first and scatters it in
- * one launch.  Results agree to the FP64 rounding of the output sums.
+ * one launch.  Results agree to the FP64 rounding of the output sums.  On a
+ * GB300 the pipelined call was slower for device-resident fields (the prep's
+ * blocks take SM slots from the arithmetic-bound scatter, and each segment
+ * launch has its own tail), hence the default; host fields are always
+ * pipelined with their copies.
  */
 fwh_status fwh_set_pipeline(fwh_handle h, int enable);
 

@@ -79,7 +79,7 @@ struct fwh_ctx {
   long long tmap_rows = 0;
   long long wait_limit = 0;      // bound of the forward pipeline waits (0: default)
   int withhold = 0;              // testing: the forward pipeline issues no copies
-  bool pipeline = true;          // device fields: prep of later segments overlaps the scatter
+  bool pipeline = false;         // device fields: prep of later segments overlaps the scatter
   // deferred device check: each call with device outputs copies the error flag
   // into pinned host memory; the next call (or fwh_check) reads it
   int *h_err = nullptr;
