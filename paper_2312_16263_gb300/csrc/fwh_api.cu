@@ -91,7 +91,7 @@ struct fwh_ctx {
   std::vector<int> h_nvalid;
   std::vector<double> h_tstart;
   // planner
-  int plan_win = -1, plan_ch = -1;
+  int plan_win = -1, plan_ch = -1, plan_sb = -1;
   std::vector<int> set_begin;
   int cfg = -1;  // forced/tuned forward config (-1 default)
   bool timing = false;
@@ -231,7 +231,8 @@ void obs_tiling(const fwh_ctx *h, const FwdConfig &c, int *obs_per_cta, int *gro
 // table and per-record window offsets, enqueued on `s`.
 fwh_status plan(fwh_handle h, const FwdConfig &c, cudaStream_t s) {
   const int ch = 32 * c.tk;
-  if (h->plan_win == c.win && h->plan_ch == ch) return FWH_OK;
+  const int sb = c.acc == 5 ? 8 : 4;  // bytes per FP32 window slot (sum, or sum + compensation)
+  if (h->plan_win == c.win && h->plan_ch == ch && h->plan_sb == sb) return FWH_OK;
   const int smax = c.win - ch - 1;
   h->set_begin = build_sets(h->y, h->P, h->mach, h->dt, smax);
   const size_t bytes = h->set_begin.size() * sizeof(int);
@@ -251,14 +252,15 @@ fwh_status plan(fwh_handle h, const FwdConfig &c, cudaStream_t s) {
   if (h->precision == FWH_FP64)
     CK(h, launch_plan<double>(reinterpret_cast<double *>(h->coef.p),
                               reinterpret_cast<const int *>(h->sets.p), nsets, (int)h->O, smax,
-                              0, reinterpret_cast<int *>(h->imax.p), h->d_err, s));
+                              0, 0, reinterpret_cast<int *>(h->imax.p), h->d_err, s));
   else
     CK(h, launch_plan<float>(reinterpret_cast<float *>(h->coef.p),
                              reinterpret_cast<const int *>(h->sets.p), nsets, (int)h->O, smax,
-                             (c.win / 2) * (int)sizeof(float),
+                             (c.win / 2) * sb, sb,
                              reinterpret_cast<int *>(h->imax.p), h->d_err, s));
   h->plan_win = c.win;
   h->plan_ch = ch;
+  h->plan_sb = sb;
   return FWH_OK;
 }
 
@@ -428,6 +430,7 @@ fwh_status run_forward(fwh_handle h, const T *d_fields, double *d_pout, cudaStre
   fa.seg_lo = 0;
   fa.seg_cnt = fa.n_segs;
   fa.win = c.win;
+  fa.wfl = c.win * (c.acc == 5 ? 2 : 1);
   if (host_fields == nullptr && (!h->pipeline || fa.n_segs < 2)) {
     CK(h, launch_prep<T>(pa, s));
     if (tev) CK(h, cudaEventRecord(tev[1], s));
@@ -792,6 +795,7 @@ fwh_status fwh_set_observers(fwh_handle h, int64_t O, const double *xyz) {
   h->O = O;
   h->nt = -1;         // window depends on the observers
   h->plan_win = -1;   // records were rewritten: window offsets must be re-planned
+  h->plan_sb = -1;
   drop_graphs(h);
   return plan_default(h);
 }
@@ -1195,6 +1199,7 @@ fwh_status batch_build(int n, const fwh_handle *hs, double *const *p_out, fwh_ha
     fa.seg_len = seg;
     fa.n_segs = bp.nseg[i];
     fa.win = c.win;
+    fa.wfl = c.win * (c.acc == 5 ? 2 : 1);
   }
   // one persistent launch per time segment over every surface's items of it
   std::vector<FwdArgs<T>> args((size_t)bp.nq * n);
@@ -1406,7 +1411,7 @@ fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, d
                 "problem needs " + std::to_string(need) + " bytes of scratch (panels x nt rounded "
                 "up to 256 x 16 values + windows); the static scratch holds " +
                     std::to_string(cap) + " bytes");
-  if (h->plan_win != c.win || h->plan_ch != 32 * c.tk)
+  if (h->plan_win != c.win || h->plan_ch != 32 * c.tk || h->plan_sb != (c.acc == 5 ? 8 : 4))
     return fail(h, FWH_ERR_STATE,
                 "the handle's panel-set plan belongs to another tile shape; call "
                 "fwh_set_tile_config (which plans without a forward pass) first");
@@ -1455,6 +1460,7 @@ fwh_status forward_into_scratch_t(fwh_handle h, const T *d_fields, int64_t nt, d
   fa.seg_lo = 0;
   fa.seg_cnt = fa.n_segs;
   fa.win = c.win;
+  fa.wfl = c.win * (c.acc == 5 ? 2 : 1);
   CK(h, launch_forward<T>(fa, c.pipe ? desc : nullptr, cfg, s));
   return defer_check(h, s);
 }

@@ -238,7 +238,8 @@ template <> __device__ __forceinline__ double int_as_rec<double>(int v) { return
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_plan(T *coef, const int *set_begin, int O, int slack,
-                                              int half_bytes, int *i0max_tab, int *err) {
+                                              int half_bytes, int slot_bytes, int *i0max_tab,
+                                              int *err) {
   const int sidx = blockIdx.x;
   const int pb = set_begin[sidx], pe = set_begin[sidx + 1];
   for (int o = threadIdx.x; o < O; o += blockDim.x) {
@@ -256,8 +257,8 @@ __global__ void __launch_bounds__(128) k_plan(T *coef, const int *set_begin, int
       rec[slot::off] = int_as_rec<T>(off);
       if (sizeof(T) == 4) {  // split window: slot x in half x & 1, word x >> 1
         const int x = off + 1, r = x & 1, q = x >> 1;
-        rec[slot::w0] = int_as_rec<T>(r * half_bytes + 4 * q);
-        rec[slot::w1] = int_as_rec<T>((1 - r) * half_bytes + 4 * (q + r));
+        rec[slot::w0] = int_as_rec<T>(r * half_bytes + slot_bytes * q);
+        rec[slot::w1] = int_as_rec<T>((1 - r) * half_bytes + slot_bytes * (q + r));
       }
     }
   }
@@ -297,7 +298,7 @@ __device__ __forceinline__ void item_prologue(const FwdArgs<T> &a, const Item<T,
   const int lane = threadIdx.x & 31;
   if (lane < it.nobs)
     s_i0max[lane] = a.i0max_tab[(size_t)it.sidx * a.O + it.o_begin + w + NW * lane];
-  for (int i = lane; i < it.nobs * a.win; i += 32) wwin[i] = T(0);
+  for (int i = lane; i < it.nobs * a.wfl; i += 32) wwin[i] = T(0);
   __syncwarp();
 }
 
@@ -392,7 +393,7 @@ __device__ __forceinline__ void process_item_direct(const FwdArgs<T> &a, int ite
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const Item<T, NW> it(a, item, w);
-  T *wwin = smem + (size_t)w * it.opw * a.win;
+  T *wwin = smem + (size_t)w * it.opw * a.wfl;
   int *s_i0max = st + w * kMaxObsPerWarp;
   item_prologue<T, NW>(a, it, w, wwin, s_i0max);
   for (int k0 = it.k_begin; k0 < it.k_end; k0 += CH) {
@@ -646,16 +647,34 @@ __device__ __forceinline__ void lds_coef(unsigned rec, Coef &k) {
   k.r1 = r.y;
 }
 
+// Value of a split-window entry: a plain FP32 sum, or a compensated pair
+// (sum, compensation) whose value is sum - compensation (formed in FP64).
+template <bool KAHAN> struct WinEntry;
+template <> struct WinEntry<false> {
+  using E = float;
+  static __device__ __forceinline__ bool nz(E e) { return e != 0.f; }
+  static __device__ __forceinline__ double value(E e) { return (double)e; }
+  static __device__ __forceinline__ E zero() { return 0.f; }
+};
+template <> struct WinEntry<true> {
+  using E = float2;
+  static __device__ __forceinline__ bool nz(E e) { return e.x != 0.f || e.y != 0.f; }
+  static __device__ __forceinline__ double value(E e) { return (double)e.x - (double)e.y; }
+  static __device__ __forceinline__ E zero() { return make_float2(0.f, 0.f); }
+};
+
 // Flush the first CH (complete) bins of every split window to p_out and slide.
-template <int CH, int NW>
+template <int CH, int NW, bool KAHAN>
 __device__ __forceinline__ void flush_slide_split(const FwdArgs<float> &a,
                                                   const Item<float, NW> &it, int w, float *wwin,
                                                   const int *s_i0max, int k0) {
+  using W = WinEntry<KAHAN>;
+  using E = typename W::E;
   const int lane = threadIdx.x & 31;
   const int H = a.win >> 1;
   for (int m = 0; m < it.nobs; ++m) {
     const int o = it.o_begin + w + NW * m;
-    float *wm = wwin + (size_t)m * a.win;
+    E *wm = reinterpret_cast<E *>(wwin + (size_t)m * a.wfl);
     const int wbase = k0 - s_i0max[m] - 1;
     const int nvalid = a.n_valid[o];
     double *po = a.p_out + (size_t)o * a.nt;
@@ -663,8 +682,8 @@ __device__ __forceinline__ void flush_slide_split(const FwdArgs<float> &a,
     for (int hf = 0; hf < 2; ++hf)
       for (int q = lane; q < CH / 2; q += 32) {
         const int bin = wbase + 2 * q + hf;
-        const float v = wm[hf * H + q];
-        if (bin >= 0 && bin < nvalid && v != 0.f) atomic_add_f64(po + bin, (double)v);
+        const E v = wm[hf * H + q];
+        if (bin >= 0 && bin < nvalid && W::nz(v)) atomic_add_f64(po + bin, W::value(v));
       }
     __syncwarp();
 #pragma unroll
@@ -673,21 +692,23 @@ __device__ __forceinline__ void flush_slide_split(const FwdArgs<float> &a,
     __syncwarp();
 #pragma unroll
     for (int hf = 0; hf < 2; ++hf)
-      for (int q = H - CH / 2 + lane; q < H; q += 32) wm[hf * H + q] = 0.f;
+      for (int q = H - CH / 2 + lane; q < H; q += 32) wm[hf * H + q] = W::zero();
     __syncwarp();
   }
 }
 
 // Segment end: the remaining split window holds partial bins of the next segment.
-template <int CH, int NW>
+template <int CH, int NW, bool KAHAN>
 __device__ __forceinline__ void flush_tail_split(const FwdArgs<float> &a,
                                                  const Item<float, NW> &it, int w, float *wwin,
                                                  const int *s_i0max) {
+  using W = WinEntry<KAHAN>;
+  using E = typename W::E;
   const int lane = threadIdx.x & 31;
   const int H = a.win >> 1;
   for (int m = 0; m < it.nobs; ++m) {
     const int o = it.o_begin + w + NW * m;
-    const float *wm = wwin + (size_t)m * a.win;
+    const E *wm = reinterpret_cast<const E *>(wwin + (size_t)m * a.wfl);
     const int wbase = it.k_end - s_i0max[m] - 1;
     const int nvalid = a.n_valid[o];
     double *po = a.p_out + (size_t)o * a.nt;
@@ -695,14 +716,37 @@ __device__ __forceinline__ void flush_tail_split(const FwdArgs<float> &a,
     for (int hf = 0; hf < 2; ++hf)
       for (int q = lane; q < H - CH / 2; q += 32) {
         const int bin = wbase + 2 * q + hf;
-        const float v = wm[hf * H + q];
-        if (bin >= 0 && bin < nvalid && v != 0.f) atomic_add_f64(po + bin, (double)v);
+        const E v = wm[hf * H + q];
+        if (bin >= 0 && bin < nvalid && W::nz(v)) atomic_add_f64(po + bin, W::value(v));
       }
   }
   __syncwarp();
 }
 
-template <int TK, int NW, bool PF, int PIPE>
+// Compensated (Kahan) update of a window entry (sum, compensation) by y.
+__device__ __forceinline__ float2 kahan_add(float2 w, float y) {
+  const float yc = __fsub_rn(y, w.y);
+  const float t = __fadd_rn(w.x, yc);
+  return make_float2(t, __fsub_rn(__fsub_rn(t, w.x), yc));
+}
+__device__ __forceinline__ float2 lds_win2(unsigned addr) {
+  float2 v;
+  asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void sts_f32x2(unsigned addr, float2 v) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void sts_f32x2_if(bool on, unsigned addr, float2 v) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %3, 0;\n\t"
+      "@p st.shared.v2.f32 [%0], {%1, %2};\n\t}" ::"r"(addr),
+      "f"(v.x), "f"(v.y), "r"((unsigned)on)
+      : "memory");
+}
+
+template <int TK, int NW, bool PF, int PIPE, bool KAHAN>
 __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
                                                  const Item<float, NW> &it,
                                                  const PipeState &ps, unsigned &step,
@@ -716,8 +760,9 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
   // Window of observer m starts at win_s + m * win_b; the record's byte
   // offsets r0 / r1 locate slots off + 1 / off + 2 of lane 0, block 0, and
   // block t adds 32 words.
-  const unsigned win_b = (unsigned)a.win * 4u;
-  const unsigned win_s = smem_u32(wwin) + (unsigned)lane * 4u;
+  constexpr unsigned EB = KAHAN ? 8u : 4u;  // bytes per window entry
+  const unsigned win_b = (unsigned)a.wfl * 4u;
+  const unsigned win_s = smem_u32(wwin) + (unsigned)lane * EB;
   const unsigned stage0 = smem_u32(ps.stage0);
   // X pair row r = lane + 32 t of a stage: 16-byte chunk c at c ^ (lane & 7).
   const unsigned xrow = (unsigned)lane * 128u;
@@ -750,46 +795,85 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
       auto observer = [&](int m, const Coef &k) {
         const unsigned base = wtok + (unsigned)m * win_b;
         const unsigned A0 = base + k.r0, A1 = base + k.r1;
-        float s0[NP], s1[NP], v0[NP];
+        if constexpr (!KAHAN) {
+          float s0[NP], s1[NP], v0[NP];
 #pragma unroll
-        for (int t = 0; t < NP; ++t) {
-          s0[t] = lds_win(A0 + 128u * t);
-          s1[t] = lds_win(A1 + 128u * t);
-        }
-        // lane 0: the slot below the chunk (other lanes read a slot of the
-        // lane below, in the window, and discard it); no lane stores to it
-        // before lane 0 does, so it is read early to hide the latency
-        const float e_old = lds_win(A1 - 4u);
-#pragma unroll
-        for (int t = 0; t < NP; ++t) {
-          float G0 = k.c[0] * X[t][0][0], M0 = k.c[0] * X[t][0][8];
-          float G1 = k.c[0] * X[t][1][0], M1 = k.c[0] * X[t][1][8];
-#pragma unroll
-          for (int q = 1; q < 8; ++q) {
-            G0 = fmaf(k.c[q], X[t][0][q], G0);
-            M0 = fmaf(k.c[q], X[t][0][8 + q], M0);
-            G1 = fmaf(k.c[q], X[t][1][q], G1);
-            M1 = fmaf(k.c[q], X[t][1][8 + q], M1);
+          for (int t = 0; t < NP; ++t) {
+            s0[t] = lds_win(A0 + 128u * t);
+            s1[t] = lds_win(A1 + 128u * t);
           }
-          // slot of the pair's first sample: both spline nodes are this lane's
-          s0[t] = fmaf(k.wdd, M1, fmaf(k.wb, G1, fmaf(k.wcc, M0, fmaf(k.wa, G0, s0[t]))));
-          // slot of the second: its left node, the right one comes from above
-          s1[t] = fmaf(k.wcc, M1, fmaf(k.wa, G1, s1[t]));
-          // right node of the pair's first sample, for the lane below
-          v0[t] = fmaf(k.wdd, M0, k.wb * G0);
+          // lane 0: the slot below the chunk (other lanes read a slot of the
+          // lane below, in the window, and discard it); no lane stores to it
+          // before lane 0 does, so it is read early to hide the latency
+          const float e_old = lds_win(A1 - 4u);
+#pragma unroll
+          for (int t = 0; t < NP; ++t) {
+            float G0 = k.c[0] * X[t][0][0], M0 = k.c[0] * X[t][0][8];
+            float G1 = k.c[0] * X[t][1][0], M1 = k.c[0] * X[t][1][8];
+#pragma unroll
+            for (int q = 1; q < 8; ++q) {
+              G0 = fmaf(k.c[q], X[t][0][q], G0);
+              M0 = fmaf(k.c[q], X[t][0][8 + q], M0);
+              G1 = fmaf(k.c[q], X[t][1][q], G1);
+              M1 = fmaf(k.c[q], X[t][1][8 + q], M1);
+            }
+            // slot of the pair's first sample: both spline nodes are this lane's
+            s0[t] = fmaf(k.wdd, M1, fmaf(k.wb, G1, fmaf(k.wcc, M0, fmaf(k.wa, G0, s0[t]))));
+            // slot of the second: its left node, the right one comes from above
+            s1[t] = fmaf(k.wcc, M1, fmaf(k.wa, G1, s1[t]));
+            // right node of the pair's first sample, for the lane below
+            v0[t] = fmaf(k.wdd, M0, k.wb * G0);
+          }
+#pragma unroll
+          for (int t = 0; t < NP; ++t) sts_f32(A0 + 128u * t, s0[t]);
+#pragma unroll
+          for (int t = 0; t + 1 < NP; ++t) {
+            // lane 0 serves lane 31 with block t + 1's first sample
+            const float x = first ? v0[t + 1] : v0[t];
+            s1[t] += __shfl_sync(0xffffffffu, x, (lane + 1) & 31);
+          }
+          s1[NP - 1] = add_from_lane_above(s1[NP - 1], v0[NP - 1]);
+#pragma unroll
+          for (int t = 0; t < NP; ++t) sts_f32(A1 + 128u * t, s1[t]);
+          sts_f32_if(first, A1 - 4u, e_old + v0[0]);  // lane 0: the slot below the chunk
+        } else {
+          // compensated: each slot is (sum, compensation); every panel's
+          // contribution to a slot is formed first, then added by Kahan's rule
+          float2 w0[NP], w1[NP];
+#pragma unroll
+          for (int t = 0; t < NP; ++t) {
+            w0[t] = lds_win2(A0 + 256u * t);
+            w1[t] = lds_win2(A1 + 256u * t);
+          }
+          const float2 e_old = lds_win2(A1 - 8u);
+          float y0[NP], y1[NP], v0[NP];
+#pragma unroll
+          for (int t = 0; t < NP; ++t) {
+            float G0 = k.c[0] * X[t][0][0], M0 = k.c[0] * X[t][0][8];
+            float G1 = k.c[0] * X[t][1][0], M1 = k.c[0] * X[t][1][8];
+#pragma unroll
+            for (int q = 1; q < 8; ++q) {
+              G0 = fmaf(k.c[q], X[t][0][q], G0);
+              M0 = fmaf(k.c[q], X[t][0][8 + q], M0);
+              G1 = fmaf(k.c[q], X[t][1][q], G1);
+              M1 = fmaf(k.c[q], X[t][1][8 + q], M1);
+            }
+            y0[t] = fmaf(k.wdd, M1, fmaf(k.wb, G1, fmaf(k.wcc, M0, k.wa * G0)));
+            y1[t] = fmaf(k.wcc, M1, k.wa * G1);
+            v0[t] = fmaf(k.wdd, M0, k.wb * G0);
+          }
+#pragma unroll
+          for (int t = 0; t < NP; ++t) sts_f32x2(A0 + 256u * t, kahan_add(w0[t], y0[t]));
+#pragma unroll
+          for (int t = 0; t + 1 < NP; ++t) {
+            const float x = first ? v0[t + 1] : v0[t];
+            y1[t] += __shfl_sync(0xffffffffu, x, (lane + 1) & 31);
+          }
+          y1[NP - 1] = add_from_lane_above(y1[NP - 1], v0[NP - 1]);
+#pragma unroll
+          for (int t = 0; t < NP; ++t) sts_f32x2(A1 + 256u * t, kahan_add(w1[t], y1[t]));
+          sts_f32x2_if(first, A1 - 8u, kahan_add(e_old, v0[0]));
         }
-#pragma unroll
-        for (int t = 0; t < NP; ++t) sts_f32(A0 + 128u * t, s0[t]);
-#pragma unroll
-        for (int t = 0; t + 1 < NP; ++t) {
-          // lane 0 serves lane 31 with block t + 1's first sample
-          const float x = first ? v0[t + 1] : v0[t];
-          s1[t] += __shfl_sync(0xffffffffu, x, (lane + 1) & 31);
-        }
-        s1[NP - 1] = add_from_lane_above(s1[NP - 1], v0[NP - 1]);
-#pragma unroll
-        for (int t = 0; t < NP; ++t) sts_f32(A1 + 128u * t, s1[t]);
-        sts_f32_if(first, A1 - 4u, e_old + v0[0]);  // lane 0: the slot below the chunk
       };
       // PF: read the next observer's record while this one computes, else
       // read each record right before its use.  A warp with the full count of
@@ -836,9 +920,9 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
         ph ^= 1u;
       }
     }
-    flush_slide_split<CH, NW>(a, it, w, wwin, s_i0max, k0);
+    flush_slide_split<CH, NW, KAHAN>(a, it, w, wwin, s_i0max, k0);
   }
-  flush_tail_split<CH, NW>(a, it, w, wwin, s_i0max);
+  flush_tail_split<CH, NW, KAHAN>(a, it, w, wwin, s_i0max);
 }
 
 // Wait until every copy the producer issued has landed, always with the full
@@ -922,8 +1006,8 @@ __device__ __forceinline__ void forward_cta(const FwdArgs<T> &a, const void *tma
       atomicMax(&issued, n0);
     }
     unsigned step = 0;
-    T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.win;
-    consume_item_f32<TK, NW, ACC == 4, 2>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
+    T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.wfl;
+    consume_item_f32<TK, NW, ACC >= 4, 2, ACC == 5>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
     __syncthreads();
     if (threadIdx.x == 0 && abort_flag) drain_copies(ps, (unsigned)issued, a.err);
   } else {
@@ -943,9 +1027,9 @@ __device__ __forceinline__ void forward_cta(const FwdArgs<T> &a, const void *tma
       }
     } else {
       const Item<T, NW> it(a, blockIdx.x, w);
-      T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.win;
+      T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.wfl;
       if constexpr (ACC >= 3 && sizeof(T) == 4) {
-        consume_item_f32<TK, NW, ACC == 4, 1>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
+        consume_item_f32<TK, NW, ACC >= 4, 1, ACC == 5>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
       } else {
         consume_item<T, TK, NW>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
       }
@@ -1015,8 +1099,8 @@ __device__ __forceinline__ void forward_batch_cta(const FwdArgs<T> *args, const 
           issue_step<T, TK, NW>(a, it, ps, j, (step + (unsigned)j) % (unsigned)nst);
         atomicMax(&issued, (int)step + n0);
       }
-      T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.win;
-      consume_item_f32<TK, NW, ACC == 4, 2>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
+      T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.wfl;
+      consume_item_f32<TK, NW, ACC >= 4, 2, ACC == 5>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
     } else {
       if (abort_flag) break;
       if (w == NW) {
@@ -1026,9 +1110,9 @@ __device__ __forceinline__ void forward_batch_cta(const FwdArgs<T> *args, const 
         }
       } else {
         const Item<T, NW> it(a, li, w);
-        T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.win;
+        T *wwin = reinterpret_cast<T *>(wbase) + (size_t)w * it.opw * a.wfl;
         if constexpr (ACC >= 3 && sizeof(T) == 4) {
-          consume_item_f32<TK, NW, ACC == 4, 1>(a, it, ps, step, wwin,
+          consume_item_f32<TK, NW, ACC >= 4, 1, ACC == 5>(a, it, ps, step, wwin,
                                                   st + w * kMaxObsPerWarp);
         } else {
           consume_item<T, TK, NW>(a, it, ps, step, wwin, st + w * kMaxObsPerWarp);
@@ -1076,6 +1160,8 @@ constexpr FwdConfig kCfgF32[] = {
     {1, 4, 4, 9, 224, 8, 3, 4, 0},
     {1, 4, 4, 9, 160, 4, 4, 4, 0},
     {1, 4, 4, 9, 224, 4, 2, 4, 0},
+    {1, 4, 4, 9, 160, 4, 2, 5, 0},
+    {1, 4, 4, 9, 224, 4, 3, 5, 0},
 };
 constexpr bool f32_obs_fit() {
   for (const FwdConfig &c : kCfgF32)
@@ -1093,7 +1179,7 @@ const FwdConfig kCfgF64[] = {
 template <typename T>
 size_t smem_for(const FwdConfig &c, int obs_per_cta) {
   const int opw = obs_per_cta / c.warps;
-  size_t win = (size_t)c.warps * opw * c.win * sizeof(T);
+  size_t win = (size_t)c.warps * opw * c.win * sizeof(T) * (c.acc == 5 ? 2 : 1);
   if (c.pipe == 0) return win;
   const size_t xb = (size_t)32 * c.tk * kRec * sizeof(T);
   const size_t sb =
@@ -1185,6 +1271,7 @@ bool encode_x_tensor_map(void *out128, const void *X, unsigned long long rows, b
       if (c.pipe == 2 && c.tk == 4 && c.warps == 8 && c.acc == 4) return CALL(T, 4, 8, 2, 4); \
       if (c.pipe == 1 && c.tk == 4 && c.warps == 4 && c.acc == 3) return CALL(T, 4, 4, 1, 3); \
       if (c.pipe == 1 && c.tk == 4 && c.warps == 4 && c.acc == 4) return CALL(T, 4, 4, 1, 4); \
+      if (c.pipe == 1 && c.tk == 4 && c.warps == 4 && c.acc == 5) return CALL(T, 4, 4, 1, 5); \
       if (c.pipe == 1 && c.tk == 8 && c.warps == 4 && c.acc == 3) return CALL(T, 8, 4, 1, 3); \
     } else {                                                                             \
       if (c.pipe == 0 && c.tk == 2 && c.warps == 8) return CALL(T, 2, 8, 0, 0);          \
@@ -1249,15 +1336,17 @@ template cudaError_t forward_batch_occupancy<double>(int, int *);
 
 template <typename T>
 cudaError_t launch_plan(T *coef, const int *set_begin, int nsets, int O, int slack,
-                        int half_bytes, int *i0max_tab, int *err, cudaStream_t s) {
+                        int half_bytes, int slot_bytes, int *i0max_tab, int *err,
+                        cudaStream_t s) {
   if (nsets <= 0 || O <= 0) return cudaSuccess;
-  k_plan<T><<<nsets, 128, 0, s>>>(coef, set_begin, O, slack, half_bytes, i0max_tab, err);
+  k_plan<T><<<nsets, 128, 0, s>>>(coef, set_begin, O, slack, half_bytes, slot_bytes, i0max_tab,
+                                  err);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_plan<float>(float *, const int *, int, int, int, int, int *, int *,
-                                        cudaStream_t);
-template cudaError_t launch_plan<double>(double *, const int *, int, int, int, int, int *,
+template cudaError_t launch_plan<float>(float *, const int *, int, int, int, int, int, int *,
+                                        int *, cudaStream_t);
+template cudaError_t launch_plan<double>(double *, const int *, int, int, int, int, int, int *,
                                          int *, cudaStream_t);
 template cudaError_t launch_forward<float>(const FwdArgs<float> &, const void *, int,
                                            cudaStream_t);

@@ -96,6 +96,8 @@ struct FwdArgs {
   int seg_len, n_segs;
   int seg_lo, seg_cnt;  // this launch covers time segments [seg_lo, seg_lo + seg_cnt)
   int win;              // window slots per observer
+  int wfl;              // values per observer window: win, or 2 win for compensated
+                        // FP32 windows (a sum and its compensation per slot)
   long long wait_cycles; // bound of each pipeline wait in SM clocks (the handle's limit)
   int withhold;         // testing: the copy pipeline issues no copies (every wait runs out)
 };
@@ -151,8 +153,9 @@ struct FwdConfig {
   int win;            // window slots per observer
   int seg_chunks;     // chunks per time segment
   int stages;         // pipeline stages (pipe = 1)
-  int acc;            // 0: one sample per lane per block, 3: FP32 sample pairs 32 apart,
-                      // 4: packed with the next record read ahead
+  int acc;            // 0: one sample per lane per block (FP64); FP32 consecutive sample
+                      // pairs with split windows: 3 plain, 4 with the next record read
+                      // ahead, 5 read ahead with compensated (Kahan) window sums
   int wide;           // 1: register cap 200 instead of the occupancy launch bound
 };
 // Bytes of dynamic shared memory a config needs for `obs_per_cta` observers.
@@ -175,11 +178,12 @@ cudaError_t launch_forward(const FwdArgs<T> &a, const void *tmap128, int cfg_idx
 // i0max_tab and, per record, the window offset i0max - i0 clamped to
 // [0, slack] (slack = win - chunk - 1) into slot 13 and, for FP32 records,
 // the split-window byte offsets of slots off + 1 and off + 2 into slots 14
-// and 15 (half_bytes: bytes of one window half); a set whose shifts span
-// more than slack raises kErrWindow.
+// and 15 (half_bytes: bytes of one window half, slot_bytes: bytes per slot);
+// a set whose shifts span more than slack raises kErrWindow.
 template <typename T>
 cudaError_t launch_plan(T *coef, const int *set_begin, int nsets, int O, int slack,
-                        int half_bytes, int *i0max_tab, int *err, cudaStream_t s);
+                        int half_bytes, int slot_bytes, int *i0max_tab, int *err,
+                        cudaStream_t s);
 
 // Batched persistent forward.
 template <typename T>

@@ -337,3 +337,33 @@ def test_oversized_mixed_problem_is_refused_and_the_handle_survives(dev):
     s.check()
     assert torch.isfinite(p).all()
     s.close()
+
+
+@pytest.mark.parametrize("kahan_cfg", [10, 11])
+def test_compensated_window_sums_stress(dev, kahan_cfg):
+    """Long in-set sums: low Mach and a coarse step keep the arrival spread of
+    a panel set small, so sets fill to their 64-panel cap and every window
+    slot sums about 128 terms per set in FP32.  The plain and the compensated
+    (Kahan) window sums both meet the mixed bar against the oracle; the
+    compensated sums are at least as accurate and agree with the FP64 path to
+    within the FP32 arithmetic of the integrands."""
+    from paper_2312_16263_gb300 import FWH
+    surf = uv_sphere(1.0, 64, 128)                       # 8192 panels
+    mach, aoa, dt, nt = 0.1, 3 * DEG, 0.05, 700
+    obs = observers_circle(60.0, 6)
+    rng = np.random.default_rng(21)
+    f = surface_fields("monopole", surf.centroids, FlowCase(mach, aoa), 0.01, 2 * np.pi, dt, nt)
+    f += rng.normal(size=f.shape) * 2e-3                 # broadband noise: cancelling terms
+    s = FWH(surf.centroids, surf.normals, surf.areas, mach, aoa, dt, "mixed", observers=obs)
+    fd = torch.as_tensor(f, dtype=torch.float32, device=dev)
+    orc = Oracle(surf.centroids, surf.normals, surf.areas, mach, aoa, dt)
+    p_ref, _, nv_ref = orc.forward(fd.double().cpu().numpy(), obs)
+    _, nv = s.window(nt)
+    errs = {}
+    for cfg in (0, kahan_cfg):
+        s.set_tile_config(cfg)
+        p = s.forward(fd).cpu().numpy()
+        s.check()
+        errs[cfg] = _compare(p, nv, p_ref, nv_ref, TOL["mixed"], f"config {cfg}")
+    assert errs[kahan_cfg] <= 1.5 * errs[0] + 1e-9, errs
+    s.close()
