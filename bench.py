@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the extra legs (workloads 1, 3, 4 backward, 5 batched, PSD)")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: workload 2 with --nt steps, two forward calls")
     ap.add_argument("--nt", type=int, default=512)
@@ -266,6 +268,140 @@ def cpu_baseline(w, target_s=15.0):
                       f"{dt:.1f} s)"}, (pick, p, nv)
 
 
+def _time_calls(fn, n, warm=2):
+    """Average ms of fn() over n calls (CUDA events on the current stream)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(n):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def _oracle_leg(w, f64_host, pick):
+    """The oracle on a sample of observers: (p_ref, nv_ref, evals/s, threads)."""
+    from oracle import Oracle
+    from oracle.oracle import max_threads
+    orc = Oracle.from_workload(w)
+    t0 = time.perf_counter()
+    p_ref, _, nv_ref = orc.forward(f64_host, w.observers[pick])
+    dt_s = time.perf_counter() - t0
+    return p_ref, nv_ref, w.surface.n_panels * w.nt * len(pick) / dt_s, max_threads()
+
+
+def extra_legs(dev):
+    """Workloads 1 (plain FP64), 3 (mixed and FP64), 4 (backward), 5 (eight
+    surfaces, batched) and the PSD of workload 2's signals, each timed with
+    CUDA events on inputs resident in HBM, with the error against the oracle on
+    a sample of observers and the oracle's rate on this host (SURVEY-style
+    side-by-side).  Returns a dict of keys for the JSON line."""
+    import numpy as np
+    import torch
+    from fwh_inputs import batch_workloads, workload
+    from paper_2312_16263_gb300 import FWH, batch_forward, welch_psd
+    out = {}
+    # workload 1: plain FP64 (and mixed), every observer against the oracle
+    w = workload(1)
+    f = w.fields(device=dev, dtype="float64")
+    p_ref, nv_ref, orate, thr = _oracle_leg(w, f.cpu().numpy(), np.arange(w.observers.shape[0]))
+    leg = {"workload": w.name, "evals": w.evals, "oracle_evals_per_s": orate, "oracle_cores": thr}
+    for prec in ("fp64", "mixed"):
+        s = FWH.from_workload(w, prec)
+        fx = f if prec == "fp64" else f.float()
+        o = torch.empty((s.O, w.nt), dtype=torch.float64, device=dev)
+        ms = _time_calls(lambda: s.forward(fx, o), 20)
+        _, nv = s.window(w.nt)
+        leg[prec] = {"ms": ms, "evals_per_s": w.evals / (ms / 1e3),
+                     "rel_l2_vs_oracle": rel_l2_stats(o.cpu().numpy(), nv, p_ref, nv_ref,
+                                                      np.arange(w.observers.shape[0]))}
+        s.check()
+        s.close()
+    out["workload1"] = leg
+    # workload 3: the contour with broadband fields, two observers against the oracle
+    w = workload(3)
+    f = w.fields(device=dev, dtype="float32")
+    pick = np.array([0, 23])
+    p_ref, nv_ref, orate, thr = _oracle_leg(w, f.double().cpu().numpy(), pick)
+    leg = {"workload": w.name, "evals": w.evals, "oracle_evals_per_s": orate, "oracle_cores": thr,
+           "oracle_sample": "observers 0 and 23, all panels and steps"}
+    for prec in ("mixed", "fp64"):
+        s = FWH.from_workload(w, prec)
+        fx = f if prec == "mixed" else f.double()
+        o = torch.empty((s.O, w.nt), dtype=torch.float64, device=dev)
+        ms = _time_calls(lambda: s.forward(fx, o), 5 if prec == "mixed" else 2, warm=1)
+        _, nv = s.window(w.nt)
+        leg[prec] = {"ms": ms, "evals_per_s": w.evals / (ms / 1e3),
+                     "rel_l2_vs_oracle": rel_l2_stats(o.cpu().numpy(), nv, p_ref, nv_ref, pick)}
+        s.check()
+        s.close()
+        del fx
+    out["workload3"] = leg
+    del f
+    # workload 4: the adjoint (d sum p^2 / d fields), against the oracle's FP64 adjoint
+    from oracle import Oracle
+    w = workload(4)
+    f = w.fields(device=dev, dtype="float32")
+    leg = {"workload": w.name, "evals": w.evals}
+    s64 = FWH.from_workload(w, "fp64")
+    g_p = 2.0 * s64.forward(f.double())
+    t0 = time.perf_counter()
+    g_ref = Oracle.from_workload(w).backward(f.double().cpu().numpy(), w.observers,
+                                             g_p.cpu().numpy())
+    leg["oracle_evals_per_s"] = w.evals / (time.perf_counter() - t0)
+    for prec in ("mixed", "fp64"):
+        s = FWH.from_workload(w, prec)
+        fx = f if prec == "mixed" else f.double()
+        gout = torch.empty_like(fx)
+        ms = _time_calls(lambda: s.backward(fx, g_p, gout), 10 if prec == "mixed" else 2, warm=1)
+        g = gout.double().cpu().numpy()
+        leg[prec] = {"ms": ms, "evals_per_s": w.evals / (ms / 1e3),
+                     "grad_rel_l2_vs_oracle": float(np.linalg.norm(g - g_ref) /
+                                                    np.linalg.norm(g_ref))}
+        s.check()
+        s.close()
+    s64.close()
+    out["backward"] = leg
+    del f, g_p
+    torch.cuda.empty_cache()
+    # workload 5: eight uneven surfaces, one graph of per-segment persistent
+    # launches with the series streamed through a two-segment ring, against
+    # one fwh_forward call per surface; the smallest surface against the oracle
+    ws5 = batch_workloads()
+    surfs = [FWH.from_workload(x, "mixed") for x in ws5]
+    fields = [x.fields(device=dev, dtype="float32") for x in ws5]
+    ev5 = sum(x.evals for x in ws5)
+    outs = batch_forward(surfs, fields)
+    ms_b = _time_calls(lambda: batch_forward(surfs, fields, outs), 3, warm=1)
+    surfs[0].check()
+    free_b = torch.cuda.mem_get_info()[0]
+    small = len(ws5) - 1
+    pick = np.array([0, ws5[small].observers.shape[0] // 2])
+    p_ref, nv_ref, orate, thr = _oracle_leg(ws5[small], fields[small].double().cpu().numpy(), pick)
+    _, nv = surfs[small].window(ws5[small].nt)
+    err_b = rel_l2_stats(outs[small].cpu().numpy(), nv, p_ref, nv_ref, pick)
+    ms_s = _time_calls(lambda: [sx.forward(fx, ox) for sx, fx, ox in zip(surfs, fields, outs)],
+                       2, warm=1)
+    free_s = torch.cuda.mem_get_info()[0]
+    out["batch"] = {"workload": "eight surfaces, 524288 panels x 4096 steps x 1024 observers each",
+                    "evals": ev5, "ms": ms_b, "evals_per_s": ev5 / (ms_b / 1e3),
+                    "per_surface_calls_ms": ms_s, "per_surface_evals_per_s": ev5 / (ms_s / 1e3),
+                    "device_free_gb_batched": free_b / 1e9,
+                    "device_free_gb_after_per_surface_calls": free_s / 1e9,
+                    "mixed_vs_oracle_rel_l2": err_b, "oracle_evals_per_s": orate,
+                    "oracle_sample": f"surface {small} ({ws5[small].surface.n_panels} panels), "
+                                     "2 observers"}
+    for sx in surfs:
+        sx.close()
+    del surfs, fields, outs
+    torch.cuda.empty_cache()
+    return out
+
+
 def rel_l2_stats(p_gpu, nv_gpu, p_ref, nv_ref, idx):
     import numpy as np
     errs = []
@@ -394,6 +530,8 @@ def main():
     fwd64 = tt64["forward_ms"] / max(1, tt64["calls"])
     p64 = out64.cpu().numpy()
     s64.check()
+    s64.close()
+    del f64, out64
     den = np.linalg.norm(p64, axis=1)
     rel_mixed_fp64 = np.linalg.norm(p_mixed - p64, axis=1) / np.where(den > 0, den, 1)
 
@@ -457,6 +595,19 @@ def main():
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }
+    # PSD of the far-field signals (Sec. IV C): Welch, 512-sample segments
+    from paper_2312_16263_gb300 import welch_psd
+    from oracle.psd import observer_psd
+    psd_ms = _time_calls(lambda: welch_psd(out, 1.0 / w.dt, 512, nv), 20)
+    psd_gpu = welch_psd(out, 1.0 / w.dt, 512, nv).cpu().numpy()
+    psd_ref = observer_psd(p_mixed, nv, 1.0 / w.dt, 512)
+    line["psd"] = {"kernel": "k_psd", "ms": psd_ms, "signals": int(s.O), "nperseg": 512,
+                   "rel_err_vs_oracle_max": float(np.nanmax(np.abs(psd_gpu - psd_ref)) /
+                                                  np.nanmax(np.abs(psd_ref)))}
+    if rank == 0 and ws == 1 and not args.no_extra:
+        del fh, oh
+        torch.cuda.empty_cache()
+        line.update(extra_legs(dev))
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, (pick, p_ref, nv_ref) = cpu_baseline(w)
         line["cpu_baseline"] = cb
@@ -465,7 +616,6 @@ def main():
     if rank == 0:
         print(json.dumps(line), flush=True)
     s.close()
-    s64.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
