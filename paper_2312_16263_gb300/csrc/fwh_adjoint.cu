@@ -122,11 +122,26 @@ __global__ void __launch_bounds__(256) k_adjoint(const T *coef, const T *Gt, T *
 // turn and, for every observer of the group, reads the two bins of each of
 // its samples from that window (conflict-free, consecutive lanes at
 // consecutive slots) and accumulates the 16 components of Xbar in registers.
-// One observer group writes Xbar directly; several add their partial sums
-// with vector atomics into a zeroed Xbar.
+// Each warp stages the group's records of its next panel in shared memory
+// (cp.async, a double buffer per warp) while it works on the current one, so
+// the inner loop reads every record as a shared-memory broadcast instead of
+// waiting on L2.  One observer group writes Xbar directly; several add their
+// partial sums with vector atomics into a zeroed Xbar.
 constexpr int kAdjGroup = 36;    // observers per item
 constexpr int kAdjWarps = 4;
 constexpr int kAdjTK = 4;        // samples per lane (chunk 128)
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 __device__ __forceinline__ void red_add_v4(float *addr, float4 v) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(addr), "f"(v.x), "f"(v.y),
@@ -137,7 +152,7 @@ __device__ __forceinline__ void red_add_v4(float *addr, float4 v) {
 template <bool kAtomic>
 __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint_set(AdjArgs<float> a) {
   constexpr int CH = 32 * kAdjTK;
-  extern __shared__ __align__(16) float gw[];  // [kAdjGroup][wstride]
+  extern __shared__ __align__(16) float gw[];  // [kAdjGroup][wstride], then the record buffers
   const int wstride = (a.win + 1 + 3) & ~3;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
@@ -161,24 +176,36 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint_set(AdjArgs<float> a
       gw[o * wstride + t] = (j >= 0 && j < a.ntp) ? G[j] : 0.f;
     }
   }
+  // this warp's record double buffer: [2][kAdjGroup][kRec]
+  float *rb = gw + (size_t)kAdjGroup * wstride + (size_t)w * 2 * kAdjGroup * kRec;
+  auto stage = [&](int p, int buf) {  // the group's records of panel p, 16 bytes a copy
+    const float *src = a.coef + ((size_t)p * a.O + o0) * kRec;
+    float *dst = rb + (size_t)buf * kAdjGroup * kRec;
+    for (int c = lane; c < no * (kRec / 4); c += 32) cp_async16(dst + 4 * c, src + 4 * c);
+    cp_async_commit();
+  };
+  int buf = 0;
+  if (p_begin + w < p_end) stage(p_begin + w, 0);
   __syncthreads();
   for (int p = p_begin + w; p < p_end; p += kAdjWarps) {
+    const bool more = p + kAdjWarps < p_end;
+    if (more) {
+      stage(p + kAdjWarps, buf ^ 1);
+      cp_async_wait<1>();  // this panel's copy has landed (the next one may still fly)
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();
     float acc[kAdjTK][kRec];
 #pragma unroll
     for (int j = 0; j < kAdjTK; ++j)
 #pragma unroll
       for (int s = 0; s < kRec; ++s) acc[j][s] = 0.f;
-    const float4 *rec = reinterpret_cast<const float4 *>(a.coef + ((size_t)p * a.O + o0) * kRec);
-    // the next observer's record is loaded while this one is accumulated
-    float4 n0 = __ldg(rec), n1 = __ldg(rec + 1), n2 = __ldg(rec + 2), n3 = __ldg(rec + 3);
+    const float4 *rec = reinterpret_cast<const float4 *>(rb + (size_t)buf * kAdjGroup * kRec);
+#pragma unroll 2
     for (int o = 0; o < no; ++o) {
-      const float4 r0 = n0, r1 = n1, r2 = n2, r3 = n3;
-      if (o + 1 < no) {
-        n0 = __ldg(rec + 4 * o + 4);
-        n1 = __ldg(rec + 4 * o + 5);
-        n2 = __ldg(rec + 4 * o + 6);
-        n3 = __ldg(rec + 4 * o + 7);
-      }
+      const float4 r0 = rec[4 * o], r1 = rec[4 * o + 1], r2 = rec[4 * o + 2],
+                   r3 = rec[4 * o + 3];
       const float c[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
       const float wa = r2.x, wb = r2.y, wcc = r2.z, wdd = r2.w;  // slots a, b, cc, dd
       const int off = __float_as_int(r3.y);                       // slot off = i0max - i0
@@ -209,6 +236,8 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint_set(AdjArgs<float> a
         else
           *reinterpret_cast<float4 *>(dst) = v;
       }
+    __syncwarp();  // every lane is done with this buffer before it is refilled
+    buf ^= 1;
   }
 }
 
@@ -231,7 +260,8 @@ cudaError_t launch_adjoint(const AdjArgs<T> &a, cudaStream_t s) {
       const long items = (long)a.nsets * ng * (a.ntp / SCH);
       if (items <= 0) return cudaSuccess;
       if (items > INT32_MAX) return cudaErrorInvalidValue;
-      const size_t smem = (size_t)kAdjGroup * ((a.win + 1 + 3) & ~3) * sizeof(float);
+      const size_t smem = ((size_t)kAdjGroup * ((a.win + 1 + 3) & ~3) +
+                           (size_t)kAdjWarps * 2 * kAdjGroup * kRec) * sizeof(float);
       if (ng > 1) {
         e = cudaMemsetAsync(a.Xbar, 0, (size_t)a.P * a.ntp * kRec * sizeof(float), s);
         if (e != cudaSuccess) return e;
