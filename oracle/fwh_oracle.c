@@ -604,3 +604,188 @@ int fwho_max_threads(void) {
   return 1;
 #endif
 }
+
+/* ======================================================================== */
+/* General moving surface: Eqs. pT and pL of Sec. II B (Farassat 1A for a   */
+/* permeable surface moving in a medium at rest), retarded time Eq. tau.    */
+/* ======================================================================== */
+/*
+ * Panels p with per-frame centroid y_p(tau_i), unit normal n_p(tau_i) and
+ * velocity v_p(tau_i) ([nt][P][3] each) and a constant area dS_p; a medium at
+ * rest with density rho0 and sound speed c0; per frame the density pulsation
+ * rho', the fluid velocity u (in the medium's frame) and p' ([nt][5][P]).
+ * Observers start at x0_o and move with one constant velocity w (w = 0: at
+ * rest; |w| < c0).  For (p, o, i), with b = x0_o + w tau_i - y_p(tau_i):
+ *   the delay Delta >= 0 of |b + w Delta| = c0 Delta (Eq. tau, r = c0 (t - tau)),
+ *   r = c0 Delta, r-hat = (b + w Delta) / r, arrival t_i = tau_i + Delta;
+ *   M = v / c0, M-dot = (dv/dtau) / c0, M_r = M.r-hat (Eq. Mr), M-dot_r =
+ *   M-dot.r-hat, M^2 = M.M, D = 1 - M_r;
+ *   Q_n = [rho0 v + rho (u - v)].n (Eq. Qn, rho = rho0 + rho'), whose source-time
+ *   derivative is the Q-dot_i n_i + Q_i n-dot_i of Eq. pT;
+ *   L_i = p' n_i + rho u_i (u.n - v.n) (Eq. Li, P_ij = p' delta_ij), L_r = L.r-hat
+ *   (Eq. Lr), L-dot_r = L-dot.r-hat, L_M = L.M (Eq. LM);
+ *   g_i = dS / (4 pi) [ Qdot_n / (r D^2) + Q_n (r Mdot_r + c0 (M_r - M^2)) / (r^2 D^3)
+ *         + Ldot_r / (c0 r D^2) + (L_r - L_M) / (r^2 D^2)
+ *         + L_r (r Mdot_r + c0 (M_r - M^2)) / (c0 r^2 D^3) ].
+ * Source-time derivatives by the second-order differences of Sec. III B.
+ * Observer window: t_start = max_p t_p(tau_0), t_end = min_p t_p(tau_max),
+ * N_o = floor((t_end - t_start) / dt) + 1, t_j = t_start + j dt (the moving-
+ * surface generalisation of Eqs. t_start, t_end).  Each panel's g and t are
+ * natural cubic splines over tau; for bin j, tau* with t(tau*) = t_j lies in
+ * the interval whose arrival times bracket t_j and is found there by
+ * bisection on the spline of t; p_j += g-spline(tau*).  Subsonic motion
+ * (|M_r| < 1) keeps t increasing in tau.
+ */
+
+typedef struct {
+  int64_t P, nt, O;
+  const double *y, *n, *v, *dS, *x0, *w;
+  double c0, rho0, dt;
+} mprob_t;
+
+/* Delay, distance and unit radiation vector of one source sample. */
+static void moving_arrival(const mprob_t *pb, const double x0[3], double tau,
+                           const double y[3], double *delay, double *r, double rh[3]) {
+  double b[3];
+  for (int c = 0; c < 3; ++c) b[c] = x0[c] + pb->w[c] * tau - y[c];
+  const double ww = pb->w[0] * pb->w[0] + pb->w[1] * pb->w[1] + pb->w[2] * pb->w[2];
+  const double bw = b[0] * pb->w[0] + b[1] * pb->w[1] + b[2] * pb->w[2];
+  const double bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  const double a = pb->c0 * pb->c0 - ww; /* > 0 */
+  /* (c0^2 - w.w) D^2 - 2 (b.w) D - b.b = 0, the non-negative root */
+  const double d = (bw + sqrt(bw * bw + a * bb)) / a;
+  *delay = d;
+  *r = pb->c0 * d;
+  for (int c = 0; c < 3; ++c) rh[c] = (b[c] + pb->w[c] * d) / *r;
+}
+
+/* Arrival time of sample i of panel p at observer o. */
+static double moving_t(const mprob_t *pb, int64_t p, int64_t o, int64_t i) {
+  double d, r, rh[3];
+  moving_arrival(pb, pb->x0 + 3 * o, (double)i * pb->dt, pb->y + (i * pb->P + p) * 3, &d, &r, rh);
+  return (double)i * pb->dt + d;
+}
+
+int fwho_forward_moving(int64_t P, int64_t nt, const double *y, const double *nrm,
+                        const double *vel, const double *areas, double c0, double rho0,
+                        double dt, const double *fields, int64_t O, const double *x0,
+                        const double *w, int n_threads, double *p_out, double *t_start,
+                        int64_t *n_valid) {
+  if (P < 1 || nt < 3 || O < 0 || !(c0 > 0.0) || !(dt > 0.0) || !(rho0 > 0.0))
+    return FWHO_ERR_ARG;
+  if (w[0] * w[0] + w[1] * w[1] + w[2] * w[2] >= c0 * c0) return FWHO_ERR_ARG;
+  mprob_t pb = {P, nt, O, y, nrm, vel, areas, x0, w, c0, rho0, dt};
+  memset(p_out, 0, sizeof(double) * (size_t)(O * nt));
+#ifdef _OPENMP
+  if (n_threads <= 0) n_threads = omp_get_max_threads();
+#else
+  n_threads = 1;
+#endif
+  for (int64_t o = 0; o < O; ++o) {
+    double ts = -INFINITY, te = INFINITY;
+    for (int64_t p = 0; p < P; ++p) {
+      const double t0 = moving_t(&pb, p, o, 0), t1 = moving_t(&pb, p, o, nt - 1);
+      if (t0 > ts) ts = t0;
+      if (t1 < te) te = t1;
+    }
+    int64_t nv = (int64_t)floor((te - ts) / dt) + 1;
+    if (nv < 0) nv = 0;
+    if (nv > nt) nv = nt;
+    t_start[o] = ts;
+    n_valid[o] = nv;
+    double *acc = (double *)calloc((size_t)(nv * n_threads + 1), sizeof(double));
+    if (!acc) return FWHO_ERR_OOM;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(n_threads)
+#endif
+    {
+#ifdef _OPENMP
+      const int tid = omp_get_thread_num();
+#else
+      const int tid = 0;
+#endif
+      double *mys = acc + nv * tid;
+      double *buf = (double *)malloc(sizeof(double) * (size_t)(20 * nt + 4));
+      double *qn = buf, *qnd = buf + nt, *L = buf + 2 * nt, *Ld = buf + 5 * nt;
+      double *vv = buf + 8 * nt, *vd = buf + 11 * nt;
+      double *g = buf + 14 * nt, *mg = buf + 15 * nt, *tt = buf + 16 * nt;
+      double *mt = buf + 17 * nt, *work = buf + 18 * nt;
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+      for (int64_t p = 0; p < P; ++p) {
+        /* Eqs. Qn, Li per frame, and the surface velocity, then their FD derivatives */
+        for (int64_t i = 0; i < nt; ++i) {
+          const double *ni = nrm + (i * P + p) * 3, *vi = vel + (i * P + p) * 3;
+          const double rho = rho0 + fields[(i * 5 + 0) * P + p];
+          const double u[3] = {fields[(i * 5 + 1) * P + p], fields[(i * 5 + 2) * P + p],
+                               fields[(i * 5 + 3) * P + p]};
+          const double pp = fields[(i * 5 + 4) * P + p];
+          double q = 0.0, un = 0.0, vn = 0.0;
+          for (int c = 0; c < 3; ++c) {
+            q += (rho0 * vi[c] + rho * (u[c] - vi[c])) * ni[c];
+            un += u[c] * ni[c];
+            vn += vi[c] * ni[c];
+          }
+          qn[i] = q;
+          for (int c = 0; c < 3; ++c) {
+            L[c * nt + i] = pp * ni[c] + rho * u[c] * (un - vn);
+            vv[c * nt + i] = vi[c];
+          }
+        }
+        fd_derivative(nt, dt, qn, 1, qnd);
+        for (int c = 0; c < 3; ++c) {
+          fd_derivative(nt, dt, L + c * nt, 1, Ld + c * nt);
+          fd_derivative(nt, dt, vv + c * nt, 1, vd + c * nt);
+        }
+        /* Eqs. pT + pL at every source sample, with its arrival time (Eq. tau) */
+        for (int64_t i = 0; i < nt; ++i) {
+          double d, r, rh[3];
+          moving_arrival(&pb, x0 + 3 * o, (double)i * dt, y + (i * P + p) * 3, &d, &r, rh);
+          double Mr = 0.0, Mdr = 0.0, M2 = 0.0, Lr = 0.0, Ldr = 0.0, LM = 0.0;
+          for (int c = 0; c < 3; ++c) {
+            const double M = vv[c * nt + i] / c0, Md = vd[c * nt + i] / c0;
+            Mr += M * rh[c];
+            Mdr += Md * rh[c];
+            M2 += M * M;
+            Lr += L[c * nt + i] * rh[c];
+            Ldr += Ld[c * nt + i] * rh[c];
+            LM += L[c * nt + i] * M;
+          }
+          const double D = 1.0 - Mr;
+          const double k = r * Mdr + c0 * (Mr - M2);
+          const double thick = qnd[i] / (r * D * D) + qn[i] * k / (r * r * D * D * D);
+          const double load = Ldr / (c0 * r * D * D) + (Lr - LM) / (r * r * D * D) +
+                              Lr * k / (c0 * r * r * D * D * D);
+          g[i] = areas[p] / (4.0 * FWHO_PI) * (thick + load);
+          tt[i] = (double)i * dt + d;
+        }
+        natural_spline_moments(nt, dt, g, mg, work);
+        natural_spline_moments(nt, dt, tt, mt, work);
+        int64_t k = 0;
+        for (int64_t j = 0; j < nv; ++j) {
+          const double tj = ts + (double)j * dt;
+          while (k < nt - 2 && tt[k + 1] < tj) ++k;
+          /* bisection on the spline of t over [tau_k, tau_k+1] */
+          double lo = (double)k * dt, hi = (double)(k + 1) * dt;
+          for (int it = 0; it < 64; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (spline_eval(nt, dt, tt, mt, mid) < tj)
+              lo = mid;
+            else
+              hi = mid;
+          }
+          mys[j] += spline_eval(nt, dt, g, mg, 0.5 * (lo + hi));
+        }
+      }
+      free(buf);
+    }
+    for (int64_t j = 0; j < nv; ++j) {
+      double s = 0.0;
+      for (int t = 0; t < n_threads; ++t) s += acc[nv * t + j];
+      p_out[o * nt + j] = s;
+    }
+    free(acc);
+  }
+  return FWHO_OK;
+}

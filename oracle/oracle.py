@@ -73,6 +73,9 @@ def load_oracle():
                 "fwho_observer_window": [ctypes.c_int64, _D, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                          ctypes.c_int64, _D, _D, _I],
+                "fwho_forward_moving": [ctypes.c_int64, ctypes.c_int64, _D, _D, _D, _D,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, _D,
+                                        ctypes.c_int64, _D, _D, ctypes.c_int, _D, _D, _I],
                 "fwho_max_threads": [],
             }
             for name, args in sigs.items():
@@ -210,6 +213,28 @@ class Oracle:
         _check(self.lib.fwho_spline_eval(y.shape[0], self.dt, _d(y), _d(m), x.shape[0],
                                          _d(x), _d(out)), "spline_eval")
         return out
+
+
+def forward_moving(y, normals, velocities, areas, c0, rho0, dt, fields, x0, w=(0.0, 0.0, 0.0),
+                   threads=0):
+    """General moving surface (Eqs. pT, pL of Sec. II B): p_out [O][nt],
+    t_start [O], n_valid [O].  y, normals, velocities: [nt][P][3]; areas [P];
+    fields [nt][5][P] (rho', u_1..3 in the medium's frame, p'); observers start
+    at x0 [O][3] and move with velocity w."""
+    lib = load_oracle()
+    y, n, v = _c64(y), _c64(normals), _c64(velocities)
+    dS, f = _c64(areas).reshape(-1), _c64(fields)
+    x = _c64(x0).reshape(-1, 3)
+    ww = _c64(w).reshape(3)
+    nt, P = y.shape[0], y.shape[1]
+    assert n.shape == y.shape and v.shape == y.shape and f.shape == (nt, 5, P)
+    O = x.shape[0]
+    p_out = np.empty((O, nt))
+    ts, nv = np.empty(O), np.empty(O, dtype=np.int64)
+    _check(lib.fwho_forward_moving(P, nt, _d(y), _d(n), _d(v), _d(dS), float(c0), float(rho0),
+                                   float(dt), _d(f), O, _d(x), _d(ww), int(threads), _d(p_out),
+                                   _d(ts), nv.ctypes.data_as(_I)), "forward_moving")
+    return p_out, ts, nv
 
 
 def max_threads() -> int:
