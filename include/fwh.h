@@ -290,6 +290,41 @@ fwh_status fwh_psd(int64_t n_sig, const double *p, int64_t ld, const int64_t *n_
                    double *psd, void *stream);
 
 /*
+ * General moving surface (Sec. II B): the permeable-surface integrals of
+ * Eqs. pT and pL (Farassat 1A) for panels moving in a medium at rest, FP64.
+ * The wind-tunnel calls above are this form seen from the surface's frame
+ * (Sec. II C); this entry point takes the motion itself.  Arguments:
+ *   y, normals, velocities [nt][P][3]: centroid, unit normal and velocity of
+ *     every panel at source time tau_i = i dt (host or device);
+ *   areas [P]: panel areas (constant);
+ *   c0, rho0: sound speed and density of the medium at rest; dt > 0;
+ *   fields [nt][5][P]: rho', u_1, u_2, u_3 (fluid velocity in the medium's
+ *     frame), p' (host or device);
+ *   x0 [O][3], w [3]: observers at x0 + w t (w = 0: at rest; |w| < c0);
+ *   p_out [O][nt] (host or device): p' at t_j = t_start + j dt for j < N_o,
+ *     0 beyond; t_start, n_valid [O] (host, may be NULL).
+ * Per (panel, observer, frame): r = c0 (t - tau) from the non-negative root of
+ * |x0 + w t - y(tau)| = c0 (t - tau) (Eq. tau), r-hat, M = v / c0, M-dot by
+ * second-order differences, Q_n = [rho0 v + rho (u - v)].n (Eq. Qn) and
+ * L_i = p' n_i + rho u_i (u.n - v.n) (Eq. Li) with their source-time
+ * derivatives, and the bracket of Eqs. pT + pL times dS / (4 pi).  Observer
+ * window: t_start = max over panels of the first frame's arrival, t_end = min
+ * of the last frame's, N_o = floor((t_end - t_start) / dt) + 1.  Each panel's
+ * signal and arrival time are natural cubic splines over tau; bin j takes the
+ * signal at the tau* whose arrival is t_j.  The motion must stay subsonic
+ * (|M_r| < 1).  Device scratch of up to about 2 GiB is taken with
+ * cudaMallocAsync on `stream`; the call synchronises.
+ * Errors: FWH_ERR_ARG (sizes, |w| >= c0, non-positive c0, rho0, dt),
+ * FWH_ERR_OOM / FWH_ERR_CUDA (message via fwh_last_error(NULL)).
+ */
+fwh_status fwh_forward_moving(int64_t n_panels, int64_t nt, const double *y,
+                              const double *normals, const double *velocities,
+                              const double *areas, double c0, double rho0, double dt,
+                              const double *fields, int64_t n_obs, const double *x0,
+                              const double *w, double *p_out, double *t_start,
+                              int64_t *n_valid, void *stream);
+
+/*
  * Measured fused multiply-add throughput of the current GPU (TFLOP/s, 2 flop
  * per FMA): FP32 for FWH_MIXED, FP64 for FWH_FP64, from independent FMA
  * chains on every SM timed with CUDA events on `stream` (about 60 ms; the

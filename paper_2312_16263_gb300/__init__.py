@@ -16,7 +16,7 @@ from .build import build  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("FWH", "batch_forward", "welch_psd"):
+    if name in ("FWH", "batch_forward", "welch_psd", "moving_forward"):
         from . import api
         return getattr(api, name)
     if name in ("fwh_apply", "FWHFunction"):
@@ -25,4 +25,5 @@ def __getattr__(name):
     raise AttributeError(name)
 
 
-__all__ = ["FWH", "batch_forward", "build", "fwh_apply", "FWHFunction", "welch_psd"]
+__all__ = ["FWH", "batch_forward", "build", "fwh_apply", "FWHFunction", "welch_psd",
+           "moving_forward"]

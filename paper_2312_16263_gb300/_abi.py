@@ -46,6 +46,9 @@ SIGNATURES = {
     "fwh_timing_totals": (ctypes.c_int, [_vp, _dp, _ip64, ctypes.c_int]),
     "fwh_check": (ctypes.c_int, [_vp, _vp]),
     "fwh_fma_peak": (ctypes.c_int, [ctypes.c_int, _dp, _vp]),
+    "fwh_forward_moving": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, _vp, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, _vp, _i64, _vp,
+                                          _vp, _vp, _dp, _ip64, _vp]),
     "fwh_psd": (ctypes.c_int, [_i64, _vp, _i64, _vp, ctypes.c_double, _i64, ctypes.c_int,
                                ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "fwh_get_sizes": (ctypes.c_int, [_vp, _ip64, _ip64, ctypes.POINTER(ctypes.c_int)]),

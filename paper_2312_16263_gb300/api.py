@@ -197,6 +197,40 @@ def welch_psd(p: torch.Tensor, fs: float, nperseg: int, n_valid=None, detrend: b
     return out
 
 
+def moving_forward(y: torch.Tensor, normals: torch.Tensor, velocities: torch.Tensor,
+                   areas, c0: float, rho0: float, dt: float, fields: torch.Tensor, x0,
+                   w=(0.0, 0.0, 0.0), out: torch.Tensor | None = None, stream=None):
+    """General moving surface (fwh_forward_moving; Eqs. pT, pL of Sec. II B).
+
+    y, normals, velocities [nt][P][3], fields [nt][5][P] float64 on one
+    device; observers at x0 [O][3] moving with w.  Returns (p_out [O][nt] on
+    the fields' device, t_start [O], n_valid [O])."""
+    nt, P = fields.shape[0], fields.shape[2]
+    for t in (y, normals, velocities):
+        if t.dtype != torch.float64 or tuple(t.shape) != (nt, P, 3) or not t.is_contiguous():
+            raise ValueError("y, normals, velocities must be contiguous [nt][P][3] float64")
+    if fields.dtype != torch.float64 or not fields.is_contiguous():
+        raise ValueError("fields must be contiguous [nt][5][P] float64")
+    dev = fields.device
+    dS = torch.as_tensor(np.asarray(areas, dtype=np.float64), device=dev).contiguous()
+    x = torch.as_tensor(np.asarray(x0, dtype=np.float64).reshape(-1, 3), device=dev).contiguous()
+    ww = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(3))
+    O = x.shape[0]
+    if out is None:
+        out = torch.empty((O, nt), dtype=torch.float64, device=dev)
+    ts = np.empty(O, dtype=np.float64)
+    nv = np.empty(O, dtype=np.int64)
+    lib = _abi.load()
+    _abi.check(lib.fwh_forward_moving(
+        P, nt, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(normals.data_ptr()),
+        ctypes.c_void_p(velocities.data_ptr()), ctypes.c_void_p(dS.data_ptr()), float(c0),
+        float(rho0), float(dt), ctypes.c_void_p(fields.data_ptr()), O,
+        ctypes.c_void_p(x.data_ptr()), ww.ctypes.data, ctypes.c_void_p(out.data_ptr()),
+        ts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        nv.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _stream_ptr(stream)))
+    return out, ts, nv
+
+
 def batch_forward(surfaces: Sequence[FWH], fields: Sequence[torch.Tensor],
                   outs: Sequence[torch.Tensor] | None = None, stream=None):
     """One persistent, graph-captured launch over several surfaces."""
