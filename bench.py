@@ -399,7 +399,58 @@ def extra_legs(dev):
         sx.close()
     del surfs, fields, outs
     torch.cuda.empty_cache()
+    out["moving"] = moving_leg(dev)
     return out
+
+
+def moving_leg(dev):
+    """The general moving-surface form (Sec. II B, fwh_forward_moving, FP64): a
+    sphere of 8192 panels spinning at 0.3 c0 around a stationary monopole,
+    2048 steps, 16 observers at rest; the oracle on one observer."""
+    import numpy as np
+    import torch
+    from fwh_inputs.geometry import observers_fibonacci, uv_sphere
+    from oracle.oracle import forward_moving
+    from paper_2312_16263_gb300 import moving_forward
+    nt, dt, Om, c0, A, om = 2048, 0.02, 0.3, 1.0, 1e-4, np.pi
+    s = uv_sphere(1.0, 64, 128)
+    P = s.n_panels
+    tau = torch.arange(nt, dtype=torch.float64, device=dev) * dt
+    c, sn = torch.cos(Om * tau), torch.sin(Om * tau)
+    rot = torch.zeros((nt, 3, 3), dtype=torch.float64, device=dev)
+    rot[:, 0, 0], rot[:, 0, 1], rot[:, 1, 0], rot[:, 1, 1], rot[:, 2, 2] = c, -sn, sn, c, 1.0
+    y = torch.einsum("tij,pj->tpi", rot, torch.as_tensor(s.centroids, device=dev)).contiguous()
+    n = torch.einsum("tij,pj->tpi", rot, torch.as_tensor(s.normals, device=dev)).contiguous()
+    v = torch.cross(torch.tensor([0.0, 0.0, Om], dtype=torch.float64, device=dev).expand_as(y), y,
+                    dim=-1).contiguous()
+    # stationary monopole (linear acoustics) sampled on the moving panels
+    r = torch.linalg.norm(y, dim=-1)
+    ph = om * (tau[:, None] - r / c0)
+    amp = A / (4 * np.pi * r)
+    e_re, e_im = amp * torch.cos(ph), amp * torch.sin(ph)
+    dr_re = -e_re / r + om / c0 * e_im          # Re[e (-1/r - i om/c0)]
+    p = om * e_im                                # -Re[i om e], rho0 = 1
+    f = torch.empty((nt, 5, P), dtype=torch.float64, device=dev)
+    f[:, 0] = p / (c0 * c0)
+    f[:, 1:4] = (dr_re[..., None] * y / r[..., None]).permute(0, 2, 1)
+    f[:, 4] = p
+    obs = observers_fibonacci(15.0, 16, np.zeros(3))
+    out = torch.empty((16, nt), dtype=torch.float64, device=dev)
+    ms = _time_calls(lambda: moving_forward(y, n, v, s.areas, c0, 1.0, dt, f, obs, out=out), 3,
+                     warm=1)
+    _, ts, nv = moving_forward(y, n, v, s.areas, c0, 1.0, dt, f, obs, out=out)
+    t0 = time.perf_counter()
+    p_ref, _, nv_ref = forward_moving(y.cpu().numpy(), n.cpu().numpy(), v.cpu().numpy(), s.areas,
+                                      c0, 1.0, dt, f.cpu().numpy(), obs[:1])
+    orate = P * nt / (time.perf_counter() - t0)
+    k = int(min(nv[0], nv_ref[0]))
+    err = float(np.linalg.norm(out[0, :k].cpu().numpy() - p_ref[0, :k]) /
+                np.linalg.norm(p_ref[0, :k]))
+    evals = P * nt * 16
+    return {"workload": "sphere 8192 panels spinning at 0.3 c0 around a monopole, 2048 steps, "
+                        "16 observers at rest (FP64)",
+            "evals": evals, "ms": ms, "evals_per_s": evals / (ms / 1e3),
+            "rel_l2_vs_oracle_observer0": err, "oracle_evals_per_s": orate}
 
 
 def rel_l2_stats(p_gpu, nv_gpu, p_ref, nv_ref, idx):

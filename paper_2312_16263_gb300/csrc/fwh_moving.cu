@@ -225,8 +225,9 @@ __global__ void __launch_bounds__(kMTile) k_mscatter(MovArgs a) {
     }
   }
   __syncthreads();
-  // signal g and arrival time t at every frame (Eqs. pT, pL, tau)
-  for (int i = 0; i < a.nt; ++i) {
+  // signal g and arrival time t at every frame (Eqs. pT, pL, tau); threads
+  // past the last panel only join the bin reductions below
+  for (int i = 0; live && i < a.nt; ++i) {
     const double tau = (double)i * a.dt;
     const double *rw = a.S + (size_t)i * kMRow * a.P + pp;
     double row[14];
@@ -253,14 +254,18 @@ __global__ void __launch_bounds__(kMTile) k_mscatter(MovArgs a) {
     G[(long)i * ld] = S4 * (thick + load);
     TT[(long)i * ld] = tau + d;
   }
-  spline_moments(G, MG, ld, a.nt, a.dt, ipiv);
-  spline_moments(TT, MT, ld, a.nt, a.dt, ipiv);
+  if (live) {
+    spline_moments(G, MG, ld, a.nt, a.dt, ipiv);
+    spline_moments(TT, MT, ld, a.nt, a.dt, ipiv);
+  }
   // observer bins: every thread walks the same j, the CTA sums its panels
   __shared__ double red[kMTile / 32];
   const int nv = a.nv[o];
   const double ts = a.ts[o], h = a.dt, h26 = a.dt * a.dt / 6.0;
   int k = 0;
   for (int j = 0; j < nv; ++j) {
+    double val = 0.0;
+    if (live) {
     const double tj = ts + (double)j * h;
     while (k < a.nt - 2 && TT[(long)(k + 1) * ld] < tj) ++k;
     const double t0 = TT[(long)k * ld], t1 = TT[(long)(k + 1) * ld];
@@ -276,9 +281,9 @@ __global__ void __launch_bounds__(kMTile) k_mscatter(MovArgs a) {
       B = fmin(1.0, fmax(0.0, B - f / df));
     }
     const double A = 1.0 - B;
-    double val = A * G[(long)k * ld] + B * G[(long)(k + 1) * ld] +
-                 ((A * A * A - A) * MG[(long)k * ld] + (B * B * B - B) * MG[(long)(k + 1) * ld]) * h26;
-    if (!live) val = 0.0;
+    val = A * G[(long)k * ld] + B * G[(long)(k + 1) * ld] +
+          ((A * A * A - A) * MG[(long)k * ld] + (B * B * B - B) * MG[(long)(k + 1) * ld]) * h26;
+    }
     for (int off = 16; off > 0; off >>= 1) val += __shfl_xor_sync(0xffffffffu, val, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = val;
     __syncthreads();
