@@ -3,9 +3,9 @@
 * the 2.5D contour with broadband fields (76800 panels x 4096 steps x 36
   observers) at full size, the oracle checking sampled observers;
 * the adjoint at the 16384-panel, 1024-step, 36-observer shape: gradients of
-  loss = sum p_out^2 against FP64 central differences (h = 1e-6) of the same
-  loss on 64 random (panel, time, field) entries, the finite differences taken
-  with the FP64 forward path (itself pinned to the oracle at 1e-10);
+  loss = sum p_out^2 against central differences of the same loss taken
+  through the oracle's forward on 64 random (panel, time, field) entries,
+  each entry above a floor held to a relative bound;
 * the eight uneven surfaces of the batched form, scaled down, through one
   persistent launch, against the oracle and against one call per surface.
 """
@@ -61,36 +61,73 @@ def test_contour_broadband_full_size_sampled(dev, prec):
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_adjoint_against_fp64_finite_differences(dev, prec):
+def test_adjoint_against_oracle_central_differences(dev, prec):
+    """dL/dfields of L = sum p_out^2 from the CUDA adjoint against central
+    differences of L taken through the oracle's forward.  The oracle's p_out
+    at the fields is the point of differentiation (and, times 2, the adjoint's
+    input).  For an entry (i, c, p) only subface p's share of p_out moves, so
+    the two perturbed losses are L(f +- h e) = sum (a + d+-)^2 with
+    a = p_out - d(f) and d the oracle's forward restricted to subface p
+    (integrands of that subface, the window of the whole surface); their
+    difference is formed as sum (d+ - d-)(2a + d+ + d-) so that it does not
+    cancel.  The integrands are cubic in the pulsations, so the central
+    difference is off by O(h^2) relative: h = 1e-4 x the component's RMS
+    balances that against rounding (about 4e-10 relative on the oracle's
+    own adjoint).  Every entry whose derivative is at least 1e-3 of
+    the largest is held to a relative bound; the rest to that bound times
+    the floor."""
     from paper_2312_16263_gb300 import FWH
     w = workload(4)
     rng = np.random.default_rng(44)
     s = FWH.from_workload(w, prec)
-    s64 = FWH.from_workload(w, "fp64")
     f = w.fields(device=dev, dtype="float64" if prec == "fp64" else "float32")
-    f64 = f.double()                       # the point both sides differentiate at
-    p = s64.forward(f64)
-    g = s.backward(f, 2.0 * p).double()    # dL/dfields, L = sum p^2
+    f64 = f.double().cpu().numpy()
+    orc = Oracle.from_workload(w)
+    obs = w.observers
+    p_ref, _, nv = orc.forward(f64, obs)
+    g = s.backward(f, torch.from_numpy(2.0 * p_ref).to(dev)).double().cpu().numpy()
     s.check()
+    s.close()
     nt, P = w.nt, w.surface.n_panels
-    ii = rng.integers(0, nt, 64)
-    cc = rng.integers(0, 5, 64)
-    pp = rng.integers(0, P, 64)
-    h = 1e-6
-    fd = np.empty(64)
-    for e in range(64):
-        x = f64.clone()
-        x[ii[e], cc[e], pp[e]] += h
-        lp = float((s64.forward(x) ** 2).sum())
-        x[ii[e], cc[e], pp[e]] -= 2 * h
-        lm = float((s64.forward(x) ** 2).sum())
-        fd[e] = (lp - lm) / (2 * h)
-    ga = g[ii, cc, pp].cpu().numpy()
+    m = 64
+    ii = rng.integers(0, nt, m)
+    cc = rng.integers(0, 5, m)
+    pp = rng.integers(0, P, m)
+    rms = np.sqrt((f64 ** 2).mean(axis=(0, 2)))
+    srf = w.surface
+    zero = np.zeros((nt, 4, P))
+    fd = np.empty(m)
+
+    def share(p, fp):
+        one = Oracle(srf.centroids[p:p + 1], srf.normals[p:p + 1], srf.areas[p:p + 1],
+                     w.mach, w.aoa, w.dt)
+        zero[:, :, p] = one.integrands(fp)[:, :, 0]
+        d = orc.forward_QL(zero, obs, p_range=(p, p + 1))[0]
+        zero[:, :, p] = 0.0
+        return d
+
+    for e in range(m):
+        i, c, p = int(ii[e]), int(cc[e]), int(pp[e])
+        h = 1e-4 * rms[c]
+        fp = f64[:, :, p:p + 1].copy()
+        a = p_ref - share(p, fp)
+        fp[i, c, 0] += h
+        dp = share(p, fp)
+        fp[i, c, 0] -= 2 * h
+        dm = share(p, fp)
+        fd[e] = float(((dp - dm) * (2 * a + dp + dm)).sum()) / (2 * h)
+    ga = g[ii, cc, pp]
     scale = np.abs(fd).max()
     assert scale > 0
-    assert np.abs(ga - fd).max() <= 1e-5 * scale, (np.abs(ga - fd).max(), scale)
-    s.close()
-    s64.close()
+    floor = 1e-3 * scale
+    big = np.abs(fd) >= floor
+    assert big.sum() >= 16, big.sum()
+    tol = 1e-8 if prec == "fp64" else 1e-4
+    rel = np.abs(ga - fd)[big] / np.abs(fd)[big]
+    print(f"[adjoint vs oracle differences, {prec}] {int(big.sum())} entries, "
+          f"relative error max {rel.max():.3e}, median {np.median(rel):.3e}")
+    assert rel.max() <= tol, (rel.max(), np.sort(rel)[-4:])
+    assert np.abs(ga - fd)[~big].max(initial=0.0) <= tol * floor
 
 
 def _host_bytes_free():
