@@ -853,15 +853,70 @@ __device__ __forceinline__ void adj_finish(const float (&z)[kAdjZ], const float 
   }
 }
 
-__global__ void __launch_bounds__(kIirThreads) k_prep_adj_iir(PrepAdjArgs<float> a) {
+// Shortest record for which one reflection at each end covers every
+// thread's filter reach [ks - 3 - H, ks + J + 2 + H] (ks < N + J): below it
+// the record ends take the general odd-periodic path.
+constexpr int kAdjOneReflect = 2 * kIirJ + kIirH + 3;
+
+// adj_finish for a thread whose reach holds a record end, unrolled like the
+// interior path (z and G stay in registers).  ks is a multiple of 32, so the
+// start end can only enter as sample 0 = ks; the far end's G is picked out
+// of the unrolled G by a select.
+__device__ __forceinline__ void adj_finish_ends(float (&z)[kAdjZ], const float *Xb, int s,
+                                                bool deriv, int ks, int N, float s6, float inv2h,
+                                                float *out /* stride 8 * kIirPanels */) {
+  constexpr int J = kIirJ;
+#pragma unroll
+  for (int t = 0; t < kAdjZ; ++t) {  // natural ends: no moment at 0 and N - 1
+    const int i = ks - 3 + t;
+    if (i <= 0 || i >= N - 1) z[t] = 0.f;
+  }
+  float G[J + 4];  // samples ks - 2 .. ks + J + 1
+#pragma unroll
+  for (int t = 0; t < J + 4; ++t) {
+    const int i = ks - 2 + t;
+    const float xv = (i >= 0 && i < N) ? Xb[(size_t)i * kRec + s] : 0.f;
+    G[t] = xv + s6 * (z[t] - 2.f * z[t + 1] + z[t + 2]);
+  }
+  float gN = 0.f;  // G at sample N - 1, when it lies in the thread's range
+#pragma unroll
+  for (int t = 0; t < J + 4; ++t)
+    if (ks - 2 + t == N - 1) gN = G[t];
+#pragma unroll
+  for (int t = 0; t < J; ++t) {
+    const int i = ks + t;
+    float c;
+    if (!deriv) {
+      c = G[t + 2];
+    } else {
+      c = 0.f;
+      if (i - 1 >= 1 && i - 1 <= N - 2) c += G[t + 1] * inv2h;
+      if (i + 1 >= 1 && i + 1 <= N - 2) c -= G[t + 3] * inv2h;
+      if (i <= 2) c += (i == 0 ? -3.f : (i == 1 ? 4.f : -1.f)) * inv2h * G[2];  // here ks = 0
+      if (i >= N - 3) c += (i == N - 1 ? 3.f : (i == N - 2 ? -4.f : 1.f)) * inv2h * gN;
+    }
+    out[t * 8 * kIirPanels] = i < N ? c : 0.f;
+  }
+}
+
+// Blocks [int_lo, int_hi) of each panel tile keep every thread's reach
+// inside rows 1 .. N - 2 (ENDS = false: the interior code alone, so its
+// register budget is not set by the record-end paths); ENDS = true runs the
+// other blocks.  1D grid, block fastest.
+template <bool ENDS>
+__global__ void __launch_bounds__(kIirThreads) k_prep_adj_iir(PrepAdjArgs<float> a, int int_lo,
+                                                              int int_hi) {
   constexpr int NP = kIirPanels, H = kIirH, J = kIirJ;
   constexpr int NR = kAdjZ + 2 * H;  // samples each thread filters
   constexpr float rho = -0.267949192431122706f;  // sqrt(3) - 2
   __shared__ float cs[kIirChunk * 8 * NP];  // [sample][series][panel]
   const int tid = threadIdx.x;
-  const int n_ct = (a.nt + kIirChunk - 1) / kIirChunk;  // 1D grid: chunk fastest
-  const int c0 = (int)(blockIdx.x % n_ct) * kIirChunk;
-  const int p0 = (int)(blockIdx.x / n_ct) * NP;
+  const int n_ct = (a.nt + kIirChunk - 1) / kIirChunk;
+  const int n_mid = int_hi - int_lo;
+  const int n_sel = ENDS ? n_ct - n_mid : n_mid;
+  const int e = (int)(blockIdx.x % n_sel);
+  const int c0 = (ENDS ? (e < int_lo ? e : e + n_mid) : int_lo + e) * kIirChunk;
+  const int p0 = (int)(blockIdx.x / n_sel) * NP;
   const int N = a.nt;
   if (c0 >= N) return;  // uniform across the CTA
   {
@@ -877,7 +932,7 @@ __global__ void __launch_bounds__(kIirThreads) k_prep_adj_iir(PrepAdjArgs<float>
     float *out = cs + (size_t)(ks - c0) * 8 * NP + s * NP + pl;
     // the filters reach samples [ks - 3 - H, ks + J + 3 + H); G reads Xbar on
     // [ks - 2, ks + J + 2)
-    const bool interior = ks - 3 - H >= 1 && ks + J + 3 + H <= N - 1;
+    const bool interior = !ENDS || (ks - 3 - H >= 1 && ks + J + 3 + H <= N - 1);
     if (interior) {
       float y[kAdjZ + H];
       float yy = 0.f;
@@ -894,6 +949,31 @@ __global__ void __launch_bounds__(kIirThreads) k_prep_adj_iir(PrepAdjArgs<float>
         if (t < kAdjZ) z[t] = -rho * xx;
       }
       adj_finish<false>(z, Xb, s, deriv, ks, N, s6, inv2h, out);
+    } else if (!ENDS) {
+      // not reached: the host gives this form interior blocks only
+    } else if (N >= kAdjOneReflect) {
+      // one reflection at each end (odd extension: zero at 0 and N - 1)
+      auto mb1 = [&](int k) -> float {
+        const bool lo = k < 0, hi = k > N - 1;
+        const int km = lo ? -k : (hi ? 2 * (N - 1) - k : k);
+        const float v = (km == 0 || km == N - 1) ? 0.f : Xb[(size_t)km * kRec + 8 + s];
+        return (lo || hi) ? -v : v;
+      };
+      float y[kAdjZ + H];
+      float yy = 0.f;
+#pragma unroll
+      for (int t = 0; t < NR; ++t) {
+        yy = mb1(ks - 3 - H + t) + rho * yy;
+        if (t >= H) y[t - H] = yy;
+      }
+      float xx = 0.f;
+      float z[kAdjZ];
+#pragma unroll
+      for (int t = kAdjZ + H - 1; t >= 0; --t) {
+        xx = y[t] + rho * xx;
+        if (t < kAdjZ) z[t] = -rho * xx;
+      }
+      adj_finish_ends(z, Xb, s, deriv, ks, N, s6, inv2h, out);
     } else {
       const int L2 = 2 * (N - 1);
       auto mb = [&](int k) -> float {  // odd-periodic extension, zero at 0 and N - 1
@@ -1032,11 +1112,23 @@ cudaError_t launch_prep(const PrepArgs<T> &a0, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_prep_adjoint(const PrepAdjArgs<T> &a0, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    const long blocks =
-        (long)((a0.nt + kIirChunk - 1) / kIirChunk) * ((a0.P + kIirPanels - 1) / kIirPanels);
-    if (blocks <= 0) return cudaSuccess;
-    if (blocks > INT32_MAX) return cudaErrorInvalidValue;
-    k_prep_adj_iir<<<(unsigned)blocks, kIirThreads, 0, s>>>(a0);
+    const int n_ct = (a0.nt + kIirChunk - 1) / kIirChunk;
+    const long tiles = (a0.P + kIirPanels - 1) / kIirPanels;
+    if (n_ct <= 0 || tiles <= 0) return cudaSuccess;
+    // interior blocks: c0 - 3 - H >= 1 and c0 + C + H + 3 <= N - 1
+    int int_lo = (kIirH + 4 + kIirChunk - 1) / kIirChunk;
+    const int top = a0.nt - 4 - kIirChunk - kIirH;  // largest interior c0
+    int int_hi = top >= 0 ? top / kIirChunk + 1 : 0;
+    if (int_hi <= int_lo) int_lo = int_hi = 0;
+    const long mid = (long)(int_hi - int_lo) * tiles;
+    const long ends = (long)(n_ct - (int_hi - int_lo)) * tiles;
+    if (mid > INT32_MAX || ends > INT32_MAX) return cudaErrorInvalidValue;
+    if (mid > 0) {
+      k_prep_adj_iir<false><<<(unsigned)mid, kIirThreads, 0, s>>>(a0, int_lo, int_hi);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    if (ends > 0) k_prep_adj_iir<true><<<(unsigned)ends, kIirThreads, 0, s>>>(a0, int_lo, int_hi);
     return cudaGetLastError();
   }
   PrepAdjArgs<T> a = a0;

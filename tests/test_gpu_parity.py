@@ -209,14 +209,14 @@ def test_host_slab_pipeline_matches_device(dev, cfg):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("n_obs", [6, 80])
-@pytest.mark.parametrize("npol,naz,nt", [(9, 13, 333), (8, 16, 90)])
+@pytest.mark.parametrize("npol,naz,nt", [(9, 13, 333), (8, 16, 83), (8, 16, 61)])
 def test_backward_matches_oracle_adjoint(dev, prec, n_obs, npol, naz, nt):
     """Adjoint vs the oracle's FP64 adjoint.  In the mixed form, 80 observers
     make three 36-observer groups whose partial gradients are added with
-    atomics (6 observers: one group, direct stores).  117 panels take the
-    4-byte field copies of the FP32 adjoint prep and 128 panels the 16-byte
-    ones; at 333 and 90 steps the last blocks' filters reflect past the
-    rows those blocks stage (and read them from global memory)."""
+    atomics (6 observers: one group, direct stores).  Two sphere meshes (117
+    and 128 panels); in the FP32 adjoint prep the record ends take one
+    reflection per end from 83 steps up (333 and 83) and the general
+    odd-periodic extension below that (61)."""
     rng = np.random.default_rng(5)
     surf = uv_sphere(1.0, npol, naz)
     mach, aoa, dt = 0.45, 8 * DEG, 0.04
