@@ -806,78 +806,66 @@ __global__ void __launch_bounds__(kThreads) k_prep_adj(PrepAdjArgs<T> a) {
 // filters samples [32 half - 3, 32 half + 35) of the tile; the per-sample
 // integrand gradients meet in shared memory and are written per (sample,
 // panel) with coalesced stores.
+//
+// Every CTA first stages in shared memory (cp.async) the moment slots of
+// its Xbar rows c0 - 3 - H .. c0 + 64 + H + 2 (the filters' reach) and, at
+// the record ends, the value slots of rows c0 - 2 .. c0 + 65.  Per panel the
+// rows are 8 floats, the panel stride padded to 8 or 24 mod 32 words so that
+// the 4 panels x 8 series one warp reads in a step sit on 32 distinct banks.
+// At the record ends the staged moments are the odd-periodic extension
+// itself (rows mapped by reflection, zero at 0 and N - 1, negated where
+// reflected) and the staged values are zero outside the record, so every
+// thread runs the same unrolled filter.  The per-sample integrand gradients
+// reuse the staging space once every thread has filtered.
 // ---------------------------------------------------------------------------
-constexpr int kAdjZ = kIirJ + 6;  // moments-adjoint values a thread keeps
+constexpr int kAdjZ = kIirJ + 6;             // moments-adjoint values a thread keeps
+constexpr int kAdjMRows = kIirRows;          // c0 - 3 - H .. c0 + C + H + 2
+constexpr int kAdjVRows = kIirChunk + 4;     // c0 - 2 .. c0 + C + 1
+constexpr int kAdjMPS = kAdjMRows * 8 + 8;   // panel strides (floats)
+constexpr int kAdjVPS = kAdjVRows * 8 + 8;
+static_assert((kAdjMPS % 32 == 8 || kAdjMPS % 32 == 24) &&
+                  (kAdjVPS % 32 == 8 || kAdjVPS % 32 == 24),
+              "bank spread of the staged rows");
+static_assert(kIirPanels * kAdjMPS >= kIirChunk * 8 * kIirPanels, "gradients fit the staging");
 
-// G and the integrand-gradient contribution of one thread's 32 samples, from
-// its kAdjZ values z (index 0 is sample ks - 3).  EDGE: record ends inside
-// the reach (compact code, z in local memory).
-template <bool EDGE>
-__device__ __forceinline__ void adj_finish(const float (&z)[kAdjZ], const float *Xb, int s,
-                                           bool deriv, int ks, int N, float s6, float inv2h,
-                                           float *out /* stride 8 * kIirPanels */) {
-  constexpr int J = kIirJ;
-  auto zf = [&](int i) -> float {
-    return (i <= 0 || i >= N - 1) ? 0.f : z[i - (ks - 3)];
-  };
-  auto Gat = [&](int i) -> float {  // 0 <= i < N, ks - 2 <= i < ks + J + 2
-    return Xb[(size_t)i * kRec + s] + s6 * (zf(i - 1) - 2.f * zf(i) + zf(i + 1));
-  };
-  if (!EDGE) {
-    float G[J + 4];  // samples ks - 2 .. ks + J + 1
-#pragma unroll
-    for (int t = 0; t < J + 4; ++t) {
-      const int i = ks - 2 + t;
-      G[t] = Xb[(size_t)i * kRec + s] + s6 * (z[t] - 2.f * z[t + 1] + z[t + 2]);
-    }
-#pragma unroll
-    for (int t = 0; t < J; ++t)
-      out[t * 8 * kIirPanels] = deriv ? (G[t + 1] - G[t + 3]) * inv2h : G[t + 2];
-  } else {
-#pragma unroll 1
-    for (int t = 0; t < J; ++t) {
-      const int i = ks + t;
-      float c = 0.f;
-      if (i < N) {
-        if (!deriv) {
-          c = Gat(i);
-        } else {
-          if (i - 1 >= 1 && i - 1 <= N - 2) c += Gat(i - 1) * inv2h;
-          if (i + 1 >= 1 && i + 1 <= N - 2) c -= Gat(i + 1) * inv2h;
-          if (i <= 2) c += (i == 0 ? -3.f : (i == 1 ? 4.f : -1.f)) * inv2h * Gat(0);
-          if (i >= N - 3) c += (i == N - 1 ? 3.f : (i == N - 2 ? -4.f : 1.f)) * inv2h * Gat(N - 1);
-        }
-      }
-      out[t * 8 * kIirPanels] = c;
-    }
-  }
+__device__ __forceinline__ void cp_async16_zfill(float *dst, const float *src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = ok ? 16 : 0;  // zero fill
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n)
+               : "memory");
 }
 
-// Shortest record for which one reflection at each end covers every
-// thread's filter reach [ks - 3 - H, ks + J + 2 + H] (ks < N + J): below it
-// the record ends take the general odd-periodic path.
-constexpr int kAdjOneReflect = 2 * kIirJ + kIirH + 3;
+// Interior thread: o[t] is the contribution of sample ks + t, from its kAdjZ
+// values z (index 0 is sample ks - 3) and the value slot s of Xbar (global).
+__device__ __forceinline__ void adj_values(const float (&z)[kAdjZ], const float *Xb, int s,
+                                           bool deriv, int ks, float s6, float inv2h,
+                                           float (&o)[kIirJ]) {
+  constexpr int J = kIirJ;
+  float G[J + 4];  // samples ks - 2 .. ks + J + 1
+#pragma unroll
+  for (int t = 0; t < J + 4; ++t)
+    G[t] = Xb[(size_t)(ks - 2 + t) * kRec + s] + s6 * (z[t] - 2.f * z[t + 1] + z[t + 2]);
+#pragma unroll
+  for (int t = 0; t < J; ++t) o[t] = deriv ? (G[t + 1] - G[t + 3]) * inv2h : G[t + 2];
+}
 
-// adj_finish for a thread whose reach holds a record end, unrolled like the
-// interior path (z and G stay in registers).  ks is a multiple of 32, so the
-// start end can only enter as sample 0 = ks; the far end's G is picked out
-// of the unrolled G by a select.
-__device__ __forceinline__ void adj_finish_ends(float (&z)[kAdjZ], const float *Xb, int s,
-                                                bool deriv, int ks, int N, float s6, float inv2h,
-                                                float *out /* stride 8 * kIirPanels */) {
+// Record-end thread: the same with the natural ends (no moment at 0 and
+// N - 1), D1^T's one-sided end rows, and zero past N - 1.  xv[8 t] is the
+// value slot of sample ks - 2 + t (zero outside the record).  ks is a
+// multiple of 32, so the start end can only enter as sample 0 = ks; the far
+// end's G is picked out of the unrolled G by a select.
+__device__ __forceinline__ void adj_values_ends(float (&z)[kAdjZ], const float *xv, bool deriv,
+                                                int ks, int N, float s6, float inv2h,
+                                                float (&o)[kIirJ]) {
   constexpr int J = kIirJ;
 #pragma unroll
-  for (int t = 0; t < kAdjZ; ++t) {  // natural ends: no moment at 0 and N - 1
+  for (int t = 0; t < kAdjZ; ++t) {
     const int i = ks - 3 + t;
     if (i <= 0 || i >= N - 1) z[t] = 0.f;
   }
   float G[J + 4];  // samples ks - 2 .. ks + J + 1
 #pragma unroll
-  for (int t = 0; t < J + 4; ++t) {
-    const int i = ks - 2 + t;
-    const float xv = (i >= 0 && i < N) ? Xb[(size_t)i * kRec + s] : 0.f;
-    G[t] = xv + s6 * (z[t] - 2.f * z[t + 1] + z[t + 2]);
-  }
+  for (int t = 0; t < J + 4; ++t) G[t] = xv[8 * t] + s6 * (z[t] - 2.f * z[t + 1] + z[t + 2]);
   float gN = 0.f;  // G at sample N - 1, when it lies in the thread's range
 #pragma unroll
   for (int t = 0; t < J + 4; ++t)
@@ -895,21 +883,23 @@ __device__ __forceinline__ void adj_finish_ends(float (&z)[kAdjZ], const float *
       if (i <= 2) c += (i == 0 ? -3.f : (i == 1 ? 4.f : -1.f)) * inv2h * G[2];  // here ks = 0
       if (i >= N - 3) c += (i == N - 1 ? 3.f : (i == N - 2 ? -4.f : 1.f)) * inv2h * gN;
     }
-    out[t * 8 * kIirPanels] = i < N ? c : 0.f;
+    o[t] = i < N ? c : 0.f;
   }
 }
 
 // Blocks [int_lo, int_hi) of each panel tile keep every thread's reach
-// inside rows 1 .. N - 2 (ENDS = false: the interior code alone, so its
-// register budget is not set by the record-end paths); ENDS = true runs the
-// other blocks.  1D grid, block fastest.
+// inside rows 1 .. N - 2 (ENDS = false); ENDS = true runs the other blocks.
+// 1D grid, block fastest.
 template <bool ENDS>
-__global__ void __launch_bounds__(kIirThreads) k_prep_adj_iir(PrepAdjArgs<float> a, int int_lo,
+__global__ void __launch_bounds__(kIirThreads, ENDS ? 5 : 7) k_prep_adj_iir(PrepAdjArgs<float> a, int int_lo,
                                                               int int_hi) {
   constexpr int NP = kIirPanels, H = kIirH, J = kIirJ;
   constexpr int NR = kAdjZ + 2 * H;  // samples each thread filters
   constexpr float rho = -0.267949192431122706f;  // sqrt(3) - 2
-  __shared__ float cs[kIirChunk * 8 * NP];  // [sample][series][panel]
+  // staged moments [NP][kAdjMPS] (later the gradients [sample][panel][series]),
+  // then, at the record ends, staged values [NP][kAdjVPS]
+  __shared__ __align__(16) float sm[NP * kAdjMPS + (ENDS ? NP * kAdjVPS : 0)];
+  float *cs = sm;
   const int tid = threadIdx.x;
   const int n_ct = (a.nt + kIirChunk - 1) / kIirChunk;
   const int n_mid = int_hi - int_lo;
@@ -919,118 +909,146 @@ __global__ void __launch_bounds__(kIirThreads) k_prep_adj_iir(PrepAdjArgs<float>
   const int p0 = (int)(blockIdx.x / n_sel) * NP;
   const int N = a.nt;
   if (c0 >= N) return;  // uniform across the CTA
+  const int L2 = 2 * (N - 1);
+  // sample k of the odd-periodic extension as a row of the record: km in
+  // [0, N - 1], reflected when the extension's sign is negative
+  auto ext_row = [&](int k, bool &reflected) -> int {
+    int km = k % L2;
+    if (km < 0) km += L2;
+    reflected = km > N - 1;
+    return reflected ? L2 - km : km;
+  };
+  if (ENDS) {
+    for (int e2 = tid; e2 < NP * 2 * kAdjMRows; e2 += kIirThreads) {
+      const int pl = e2 / (2 * kAdjMRows), rq = e2 - pl * (2 * kAdjMRows);
+      const float *xp = a.Xbar + (size_t)min(p0 + pl, a.P - 1) * a.ntp * kRec + 8 + 4 * (rq & 1);
+      bool refl;
+      const int km = ext_row(c0 - 3 - H + (rq >> 1), refl);
+      cp_async16_zfill(sm + pl * kAdjMPS + 4 * rq, xp + (size_t)km * kRec, km != 0 && km != N - 1);
+    }
+  } else {
+    // piece rq (row rq / 2, half rq % 2) of every panel: rq = tid and tid + 128
+    static_assert(2 * kAdjMRows <= 2 * kIirThreads, "two pieces per thread and panel");
+    const int rq1 = tid + kIirThreads;
+    const bool two = rq1 < 2 * kAdjMRows;
+    const size_t o0 = (size_t)(c0 - 3 - H) * kRec + 8 + (tid >> 1) * kRec + 4 * (tid & 1);
+    const size_t o1 = (size_t)(c0 - 3 - H) * kRec + 8 + (rq1 >> 1) * kRec + 4 * (rq1 & 1);
+#pragma unroll 1
+    for (int pl = 0; pl < NP; ++pl) {
+      const float *xp = a.Xbar + (size_t)min(p0 + pl, a.P - 1) * a.ntp * kRec;
+      cp_async16(sm + pl * kAdjMPS + 4 * tid, xp + o0);
+      if (two) cp_async16(sm + pl * kAdjMPS + 4 * rq1, xp + o1);
+    }
+  }
+  if (ENDS) {
+    float *sv = sm + NP * kAdjMPS;
+    for (int e2 = tid; e2 < NP * 2 * kAdjVRows; e2 += kIirThreads) {
+      const int pl = e2 / (2 * kAdjVRows), rq = e2 - pl * (2 * kAdjVRows);
+      const int i = c0 - 2 + (rq >> 1);
+      const bool in = i >= 0 && i < N;
+      const float *xp = a.Xbar + (size_t)min(p0 + pl, a.P - 1) * a.ntp * kRec + 4 * (rq & 1);
+      cp_async16_zfill(sv + pl * kAdjVPS + 4 * rq, xp + (size_t)(in ? i : 0) * kRec, in);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (ENDS) {  // negate the reflected rows
+    for (int e3 = tid; e3 < NP * kAdjMRows; e3 += kIirThreads) {
+      const int pl = e3 / kAdjMRows, r = e3 - pl * kAdjMRows;
+      bool refl;
+      ext_row(c0 - 3 - H + r, refl);
+      if (refl) {
+        float4 *q = reinterpret_cast<float4 *>(sm + pl * kAdjMPS + 8 * r);
+        const float4 u = q[0], w = q[1];
+        q[0] = make_float4(-u.x, -u.y, -u.z, -u.w);
+        q[1] = make_float4(-w.x, -w.y, -w.z, -w.w);
+      }
+    }
+    __syncthreads();
+  }
   {
     const int s = tid & 7;
     const int pl = (tid >> 3) % NP;
     const int h = tid / (8 * NP);
     const int ks = c0 + J * h;
-    const int p = min(p0 + pl, a.P - 1);
-    const float *Xb = a.Xbar + (size_t)p * a.ntp * kRec;
     const bool deriv = (s == 0) || (s >= 2 && s <= 4);
     const float inv2h = (float)(0.5 / a.dt);
     const float s6 = (float)(6.0 / (a.dt * a.dt));
-    float *out = cs + (size_t)(ks - c0) * 8 * NP + s * NP + pl;
-    // the filters reach samples [ks - 3 - H, ks + J + 3 + H); G reads Xbar on
-    // [ks - 2, ks + J + 2)
-    const bool interior = !ENDS || (ks - 3 - H >= 1 && ks + J + 3 + H <= N - 1);
-    if (interior) {
-      float y[kAdjZ + H];
-      float yy = 0.f;
+    // moment slot s of sample ks - 3 - H + t: staged row ks - c0 + t
+    const float *xm = sm + pl * kAdjMPS + (ks - c0) * 8 + s;
+    float y[kAdjZ + H];
+    float yy = 0.f;
 #pragma unroll
-      for (int t = 0; t < NR; ++t) {
-        yy = Xb[(size_t)(ks - 3 - H + t) * kRec + 8 + s] + rho * yy;
-        if (t >= H) y[t - H] = yy;
-      }
-      float xx = 0.f;
-      float z[kAdjZ];
-#pragma unroll
-      for (int t = kAdjZ + H - 1; t >= 0; --t) {
-        xx = y[t] + rho * xx;
-        if (t < kAdjZ) z[t] = -rho * xx;
-      }
-      adj_finish<false>(z, Xb, s, deriv, ks, N, s6, inv2h, out);
-    } else if (!ENDS) {
-      // not reached: the host gives this form interior blocks only
-    } else if (N >= kAdjOneReflect) {
-      // one reflection at each end (odd extension: zero at 0 and N - 1)
-      auto mb1 = [&](int k) -> float {
-        const bool lo = k < 0, hi = k > N - 1;
-        const int km = lo ? -k : (hi ? 2 * (N - 1) - k : k);
-        const float v = (km == 0 || km == N - 1) ? 0.f : Xb[(size_t)km * kRec + 8 + s];
-        return (lo || hi) ? -v : v;
-      };
-      float y[kAdjZ + H];
-      float yy = 0.f;
-#pragma unroll
-      for (int t = 0; t < NR; ++t) {
-        yy = mb1(ks - 3 - H + t) + rho * yy;
-        if (t >= H) y[t - H] = yy;
-      }
-      float xx = 0.f;
-      float z[kAdjZ];
-#pragma unroll
-      for (int t = kAdjZ + H - 1; t >= 0; --t) {
-        xx = y[t] + rho * xx;
-        if (t < kAdjZ) z[t] = -rho * xx;
-      }
-      adj_finish_ends(z, Xb, s, deriv, ks, N, s6, inv2h, out);
-    } else {
-      const int L2 = 2 * (N - 1);
-      auto mb = [&](int k) -> float {  // odd-periodic extension, zero at 0 and N - 1
-        int km = k % L2;
-        if (km < 0) km += L2;
-        float sg = 1.f;
-        if (km >= N - 1) {
-          km = L2 - km;
-          sg = -1.f;
-        }
-        if (km == 0 || km == N - 1) return 0.f;
-        return sg * Xb[(size_t)km * kRec + 8 + s];
-      };
-      float y[kAdjZ + H];
-      float yy = 0.f;
-#pragma unroll 1
-      for (int t = 0; t < NR; ++t) {
-        yy = mb(ks - 3 - H + t) + rho * yy;
-        if (t >= H) y[t - H] = yy;
-      }
-      float xx = 0.f;
-      float z[kAdjZ];
-#pragma unroll 1
-      for (int t = kAdjZ + H - 1; t >= 0; --t) {
-        xx = y[t] + rho * xx;
-        if (t < kAdjZ) z[t] = -rho * xx;
-      }
-      adj_finish<true>(z, Xb, s, deriv, ks, N, s6, inv2h, out);
+    for (int t = 0; t < NR; ++t) {
+      yy = xm[8 * t] + rho * yy;
+      if (t >= H) y[t - H] = yy;
     }
+    float xx = 0.f;
+    float z[kAdjZ];
+#pragma unroll
+    for (int t = kAdjZ + H - 1; t >= 0; --t) {
+      xx = y[t] + rho * xx;
+      if (t < kAdjZ) z[t] = -rho * xx;
+    }
+    float o[J];
+    if (ENDS) {
+      // value slot s of sample ks - 2 + t: staged row ks - c0 + t
+      adj_values_ends(z, sm + NP * kAdjMPS + pl * kAdjVPS + (ks - c0) * 8 + s, deriv, ks, N, s6,
+                      inv2h, o);
+    } else {
+      adj_values(z, a.Xbar + (size_t)min(p0 + pl, a.P - 1) * a.ntp * kRec, s, deriv, ks, s6,
+                 inv2h, o);
+    }
+    __syncthreads();  // every thread is done with the staged moments
+    // [sample][panel][series]: the warp's 4 panels x 8 series on 32 banks
+    float *out = cs + (size_t)(ks - c0) * 8 * NP + pl * 8 + s;
+#pragma unroll
+    for (int t = 0; t < J; ++t) out[t * 8 * NP] = o[t];
   }
   __syncthreads();
   // ---- integrand gradients -> field gradients, per (sample, panel) ----------
-  for (int idx = tid; idx < kIirChunk * NP; idx += kIirThreads) {
-    const int ir = idx / NP, pl = idx % NP;
-    const int i = c0 + ir, p = p0 + pl;
-    if (i >= N || p >= a.P) continue;
-    const float *c = cs + (size_t)ir * 8 * NP + pl;
-    const float qb = c[0] + c[NP];                       // Qn: series 0 and 1
-    const float lb0 = c[2 * NP] + c[5 * NP];             // L_c: series 2 + c and 5 + c
-    const float lb1 = c[3 * NP] + c[6 * NP];
-    const float lb2 = c[4 * NP] + c[7 * NP];
-    const int po = a.perm ? a.perm[p] : p;
-    const float n0 = (float)a.n[3 * p], n1 = (float)a.n[3 * p + 1], n2 = (float)a.n[3 * p + 2];
-    const float Un = (float)(a.ca * a.n[3 * p] + a.sa * a.n[3 * p + 1]);
-    const float *fb = a.fields + (size_t)i * 5 * a.P + po;
-    const float rho_ = fb[0], u0 = fb[(size_t)a.P], u1 = fb[2 * (size_t)a.P],
-                u2 = fb[3 * (size_t)a.P];
-    const float un = u0 * n0 + u1 * n1 + u2 * n2;
-    const float utn = Un + un;   // total u . n
-    const float r1 = 1.f + rho_;
-    const float lu = lb0 * u0 + lb1 * u1 + lb2 * u2;
-    float *g = a.grad_fields + (size_t)i * 5 * a.P + po;
-    g[0] = qb * utn + lu * utn;                               // d/drho'
-    g[(size_t)a.P] = r1 * (qb * n0 + lb0 * utn + lu * n0);   // d/du'_1
-    g[2 * (size_t)a.P] = r1 * (qb * n1 + lb1 * utn + lu * n1);
-    g[3 * (size_t)a.P] = r1 * (qb * n2 + lb2 * utn + lu * n2);
-    g[4 * (size_t)a.P] = lb0 * n0 + lb1 * n1 + lb2 * n2;     // d/dp' (dL_c/dp' = n_c)
+  // thread: panel tid % NP, samples tid / NP + 16 it; the field loads of all
+  // its samples are issued before any of them is used
+  {
+    constexpr int IT = kIirChunk * NP / kIirThreads;
+    constexpr int RS = kIirThreads / NP;  // sample stride
+    const int pl = tid % NP, p = p0 + pl;
+    if (p < a.P) {
+      const int po = a.perm ? a.perm[p] : p;
+      const float n0 = (float)a.n[3 * p], n1 = (float)a.n[3 * p + 1], n2 = (float)a.n[3 * p + 2];
+      const float Un = (float)(a.ca * a.n[3 * p] + a.sa * a.n[3 * p + 1]);
+      float f[IT][4];
+#pragma unroll
+      for (int it = 0; it < IT; ++it) {
+        const int i = c0 + tid / NP + RS * it;
+        const float *fb = a.fields + (size_t)min(i, N - 1) * 5 * a.P + po;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) f[it][q] = fb[(size_t)q * a.P];
+      }
+#pragma unroll
+      for (int it = 0; it < IT; ++it) {
+        const int ir = tid / NP + RS * it;
+        const int i = c0 + ir;
+        if (i >= N) continue;
+        const float4 c03 = *reinterpret_cast<const float4 *>(cs + (size_t)ir * 8 * NP + pl * 8);
+        const float4 c47 = *reinterpret_cast<const float4 *>(cs + (size_t)ir * 8 * NP + pl * 8 + 4);
+        const float qb = c03.x + c03.y;                      // Qn: series 0 and 1
+        const float lb0 = c03.z + c47.y;                     // L_c: series 2 + c and 5 + c
+        const float lb1 = c03.w + c47.z;
+        const float lb2 = c47.x + c47.w;
+        const float rho_ = f[it][0], u0 = f[it][1], u1 = f[it][2], u2 = f[it][3];
+        const float un = u0 * n0 + u1 * n1 + u2 * n2;
+        const float utn = Un + un;   // total u . n
+        const float r1 = 1.f + rho_;
+        const float lu = lb0 * u0 + lb1 * u1 + lb2 * u2;
+        float *g = a.grad_fields + (size_t)i * 5 * a.P + po;
+        g[0] = qb * utn + lu * utn;                               // d/drho'
+        g[(size_t)a.P] = r1 * (qb * n0 + lb0 * utn + lu * n0);   // d/du'_1
+        g[2 * (size_t)a.P] = r1 * (qb * n1 + lb1 * utn + lu * n1);
+        g[3 * (size_t)a.P] = r1 * (qb * n2 + lb2 * utn + lu * n2);
+        g[4 * (size_t)a.P] = lb0 * n0 + lb1 * n1 + lb2 * n2;     // d/dp' (dL_c/dp' = n_c)
+      }
+    }
   }
 }
 
