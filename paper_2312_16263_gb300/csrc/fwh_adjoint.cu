@@ -135,6 +135,12 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
+// 4-byte copy, zero fill when !ok (src is then not read)
+__device__ __forceinline__ void cp_async4_zf(float *dst, const float *src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -167,15 +173,18 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint_set(AdjArgs<float> a
   const int o0 = g * kAdjGroup;
   const int no = min(kAdjGroup, a.O - o0);
   const int p_begin = a.set_begin[sidx], p_end = a.set_begin[sidx + 1];
-  // stage the window of each observer of the group
+  // stage the window of each observer of the group (cp.async: every copy in
+  // flight at once; zero outside the record)
   for (int o = 0; o < no; ++o) {
     const int base = k0 - a.i0max_tab[(size_t)sidx * a.O + o0 + o] - 1;
     const float *G = a.Gt + (size_t)(o0 + o) * a.ntp;
     for (int t = threadIdx.x; t <= a.win; t += blockDim.x) {
       const int j = base + t;
-      gw[o * wstride + t] = (j >= 0 && j < a.ntp) ? G[j] : 0.f;
+      const bool ok = j >= 0 && j < a.ntp;
+      cp_async4_zf(gw + o * wstride + t, G + (ok ? j : 0), ok);
     }
   }
+  cp_async_commit();
   // this warp's record double buffer: [2][kAdjGroup][kRec]
   float *rb = gw + (size_t)kAdjGroup * wstride + (size_t)w * 2 * kAdjGroup * kRec;
   auto stage = [&](int p, int buf) {  // the group's records of panel p, 16 bytes a copy
@@ -186,6 +195,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint_set(AdjArgs<float> a
   };
   int buf = 0;
   if (p_begin + w < p_end) stage(p_begin + w, 0);
+  cp_async_wait<0>();  // the window (and this warp's first records)
   __syncthreads();
   for (int p = p_begin + w; p < p_end; p += kAdjWarps) {
     const bool more = p + kAdjWarps < p_end;
