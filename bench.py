@@ -357,7 +357,8 @@ def extra_legs(dev):
         s = FWH.from_workload(w, prec)
         fx = f if prec == "mixed" else f.double()
         gout = torch.empty_like(fx)
-        ms = _time_calls(lambda: s.backward(fx, g_p, gout), 10 if prec == "mixed" else 2, warm=1)
+        ms = _time_calls(lambda: s.backward(fx, g_p, gout), 20 if prec == "mixed" else 2,
+                         warm=3 if prec == "mixed" else 1)
         g = gout.double().cpu().numpy()
         leg[prec] = {"ms": ms, "evals_per_s": w.evals / (ms / 1e3),
                      "grad_rel_l2_vs_oracle": float(np.linalg.norm(g - g_ref) /

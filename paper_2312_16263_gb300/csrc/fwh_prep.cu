@@ -192,8 +192,12 @@ __global__ void __launch_bounds__(PrepTile<T>::panels * 8) k_prep(PrepArgs<T> a)
   __syncthreads();
 
   // ---- phase B: series, forward elimination, back substitution ----------------
-  const int s = tid & 7;
-  const int pl = tid >> 3;
+  // warps 0, 1: the value series (1, 5, 6, 7) of panels 0-7, 8-15; warps 2, 3:
+  // the derivative series (0, 2, 3, 4).  Lane = 4 x panel + integrand, so in
+  // an interior chunk two whole warps finish after writing their values.
+  static_assert(NP == 16 && NT == 128, "phase-B lane map");
+  const int pl = ((tid >> 5) & 1) * 8 + ((tid & 31) >> 2);
+  const int s = (tid >> 6) ? ((tid & 3) == 0 ? 0 : 1 + (tid & 3)) : ((tid & 3) == 0 ? 1 : 4 + (tid & 3));
   const int p = p0 + pl;
   if (p >= a.P) return;
   T *Xp = a.X + ((long)p * a.x_ld + xoff) * kRec;  // row i of the chunk at Xp + i kRec
@@ -207,6 +211,18 @@ __global__ void __launch_bounds__(PrepTile<T>::panels * 8) k_prep(PrepArgs<T> a)
   auto B = [&](int i) -> T { return col[(size_t)(i - ra) * 4 * NP]; };
   const T inv2h = (T)(0.5 / a.dt);
   const T s6 = (T)(6.0 / (a.dt * a.dt));
+  // Interior chunk (window rows inside 1 .. N - 2, so every derivative value
+  // in it is a central difference): the moment solve commutes with the
+  // central difference, so a derivative series' moments are the central
+  // differences of its integrand's value-series moments.  The value-series
+  // thread solves and writes both; the derivative-series thread only writes
+  // its values.  Uniform across the CTA.
+  const bool inner = wa >= 1 && ce + H <= nt - 1;
+  if (inner && deriv) {
+    for (int i = c0; i < ce; ++i) Xp[xidx<T>(i, s)] = (B(i + 1) - B(i - 1)) * inv2h;
+    return;
+  }
+  const int sd = q == 0 ? 0 : 1 + q;  // the derivative series of integrand q
   auto F = [&](int i) -> T {
     if (!deriv) return B(i);
     if (i == 0) return (T(-3) * B(0) + T(4) * B(1) - B(2)) * inv2h;
@@ -214,7 +230,7 @@ __global__ void __launch_bounds__(PrepTile<T>::panels * 8) k_prep(PrepArgs<T> a)
     return (B(i + 1) - B(i - 1)) * inv2h;
   };
   const int L = wb - wa;
-  T Fprev = T(0), Fcur = F(wa), z = T(0);
+  T Fprev = T(0), Fcur = F(wa), z = T(0), z_below = T(0);  // z_below: row c0 - 1
 #pragma unroll 4
   for (int i = wa; i < wb; ++i) {
     const int j = i - wa;
@@ -227,18 +243,27 @@ __global__ void __launch_bounds__(PrepTile<T>::panels * 8) k_prep(PrepArgs<T> a)
         zh[(size_t)(i - ce) * NT + tid] = z;
       } else if (i >= c0) {
         Xp[xidx<T>(i, 8 + s)] = z;
+      } else if (i == c0 - 1) {
+        z_below = z;
       }
     }
     Fprev = Fcur;
     Fcur = Fnext;
   }
-  T mnext = T(0);
+  // back substitution; in an interior chunk m_{i+1}' = (m_{i+2} - m_i) / (2 dt)
+  // goes to the derivative series' moment slot as m_i is found
+  T mnext = T(0), mnext2 = T(0);
+  auto emit = [&](int i, T m) {  // m = m_i, mnext2 = m_{i+2}
+    if (inner && i + 1 >= c0 && i + 1 < ce) Xp[xidx<T>(i + 1, 8 + sd)] = (mnext2 - m) * inv2h;
+  };
   if (wb - 1 >= c0 && wb - 1 < ce) Xp[xidx<T>(wb - 1, 8 + s)] = T(0);
   const int ilo = max(c0, wa + 1);
   int i = wb - 2;
   // right halo (elimination values in shared memory)
   for (; i >= ilo && i >= ce; --i) {
     const T m = zh[(size_t)(i - ce) * NT + tid] - mnext * inv_piv<T>(i - wa);
+    emit(i, m);
+    mnext2 = mnext;
     mnext = m;
   }
   // chunk: elimination values come back from X in blocks, loads issued first
@@ -251,14 +276,19 @@ __global__ void __launch_bounds__(PrepTile<T>::panels * 8) k_prep(PrepArgs<T> a)
     for (int u = 0; u < BB; ++u) {
       const T m = zb[u] - mnext * inv_piv<T>(i - u - wa);
       Xp[xidx<T>(i - u, 8 + s)] = m;
+      emit(i - u, m);
+      mnext2 = mnext;
       mnext = m;
     }
   }
   for (; i >= ilo; --i) {
     const T m = Xp[xidx<T>(i, 8 + s)] - mnext * inv_piv<T>(i - wa);
     Xp[xidx<T>(i, 8 + s)] = m;
+    emit(i, m);
+    mnext2 = mnext;
     mnext = m;
   }
+  if (inner) emit(c0 - 1, z_below - mnext * inv_piv<T>(c0 - 1 - wa));  // m_{c0-1}: row c0's
   if (wa == c0) Xp[xidx<T>(c0, 8 + s)] = T(0);  // record start: m_0 = 0
 }
 
