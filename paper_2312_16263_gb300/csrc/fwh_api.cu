@@ -1299,6 +1299,8 @@ extern "C" fwh_status fwh_batch_forward(int n, const fwh_handle *hs, const void 
   if (n < 1 || !hs || !fields || !nt || !p_out)
     return fail(nullptr, FWH_ERR_ARG, "invalid batch arguments");
   fwh_handle h0 = hs[0];
+  if (n > kMaxBatchSurf)
+    return fail(h0, FWH_ERR_ARG, "more surfaces than one batched call takes");
   if (!h0) return fail(nullptr, FWH_ERR_ARG, "NULL handle in batch");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   {

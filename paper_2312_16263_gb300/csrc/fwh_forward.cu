@@ -584,15 +584,6 @@ __device__ __forceinline__ float lds_win(unsigned addr) {
 __device__ __forceinline__ void sts_f32(unsigned addr, float v) {
   asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
-// Store by the lanes whose `on` is set (the others store nothing).
-__device__ __forceinline__ void sts_f32_if(bool on, unsigned addr, float v) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.u32 p, %2, 0;\n\t"
-      "@p st.shared.f32 [%0], %1;\n\t}" ::"r"(addr),
-      "f"(v), "r"((unsigned)on)
-      : "memory");
-}
 
 // Loads of stage data (X rows, records): not volatile, so the compiler may
 // schedule them early; they stay after the stage's full-barrier wait because
@@ -737,14 +728,6 @@ __device__ __forceinline__ float2 lds_win2(unsigned addr) {
 __device__ __forceinline__ void sts_f32x2(unsigned addr, float2 v) {
   asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
-__device__ __forceinline__ void sts_f32x2_if(bool on, unsigned addr, float2 v) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.u32 p, %3, 0;\n\t"
-      "@p st.shared.v2.f32 [%0], {%1, %2};\n\t}" ::"r"(addr),
-      "f"(v.x), "f"(v.y), "r"((unsigned)on)
-      : "memory");
-}
 
 template <int TK, int NW, bool PF, int PIPE, bool KAHAN>
 __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
@@ -835,7 +818,9 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
           s1[NP - 1] = add_from_lane_above(s1[NP - 1], v0[NP - 1]);
 #pragma unroll
           for (int t = 0; t < NP; ++t) sts_f32(A1 + 128u * t, s1[t]);
-          sts_f32_if(first, A1 - 4u, e_old + v0[0]);  // lane 0: the slot below the chunk
+          // lane 0: the slot below the chunk (a C++ condition, so the compiler
+          // predicates the store on `first` computed once, not per observer)
+          if (first) sts_f32(A1 - 4u, e_old + v0[0]);
         } else {
           // compensated: each slot is (sum, compensation); every panel's
           // contribution to a slot is formed first, then added by Kahan's rule
@@ -872,7 +857,7 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
           y1[NP - 1] = add_from_lane_above(y1[NP - 1], v0[NP - 1]);
 #pragma unroll
           for (int t = 0; t < NP; ++t) sts_f32x2(A1 + 256u * t, kahan_add(w1[t], y1[t]));
-          sts_f32x2_if(first, A1 - 8u, kahan_add(e_old, v0[0]));
+          if (first) sts_f32x2(A1 - 8u, kahan_add(e_old, v0[0]));
         }
       };
       // PF: read the next observer's record while this one computes, else
@@ -1053,12 +1038,25 @@ __global__ void __maxnreg__(200) k_forward_wide(FwdArgs<T> a,
 }
 
 // Persistent form: CTAs pull work items of several surfaces from one queue.
+// The surfaces' arguments and item offsets are copied to shared memory once
+// per CTA (kMaxBatchSurf at most; the host checks), and each CTA claims its
+// next item while it works on the current one, so an item boundary costs no
+// global-memory round trip.
 template <typename T, int TK, int NW, int PIPE, int ACC>
-__device__ __forceinline__ void forward_batch_cta(const FwdArgs<T> *args, const int *item_prefix,
-                                                  int n_surf, int total, int *counter, int nst) {
+__device__ __forceinline__ void forward_batch_cta(const FwdArgs<T> *args_g,
+                                                  const int *item_prefix_g, int n_surf, int total,
+                                                  int *counter, int nst) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int st[NW * kMaxObsPerWarp];
   __shared__ int s_item;
+  __shared__ FwdArgs<T> s_args[kMaxBatchSurf];
+  __shared__ int s_prefix[kMaxBatchSurf];
+  for (int i = threadIdx.x; i < n_surf; i += blockDim.x) {
+    s_args[i] = args_g[i];
+    s_prefix[i] = item_prefix_g[i];
+  }
+  if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+  __syncthreads();
   __shared__ __align__(8) uint64_t bars[2 * kMaxStages];
   __shared__ int abort_flag;
   __shared__ int released[kMaxStages];
@@ -1067,25 +1065,24 @@ __device__ __forceinline__ void forward_batch_cta(const FwdArgs<T> *args, const 
   unsigned char *wbase = smem_raw;
   if constexpr (PIPE != 0) {
     int maxo = 0;
-    for (int i = 0; i < n_surf; ++i) maxo = max(maxo, args[i].obs_per_cta);
+    for (int i = 0; i < n_surf; ++i) maxo = max(maxo, s_args[i].obs_per_cta);
     wbase = pipe_setup<T, TK, NW>(smem_raw, maxo, nst, bars, &abort_flag, ps,
                                   PIPE == 2 ? released : nullptr, PIPE == 2 ? &issued : nullptr);
   }
   const int w = threadIdx.x >> 5;
   unsigned step = 0;
   for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-    __syncthreads();
+    __syncthreads();  // the previous item is done; s_item holds this one
     const int item = s_item;
+    __syncthreads();  // every thread has read it
     if (item >= total) break;
     int lo = 0, hi = n_surf - 1;  // surface of this item: item_prefix[s] <= item
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (item_prefix[mid] <= item) lo = mid; else hi = mid - 1;
+      if (s_prefix[mid] <= item) lo = mid; else hi = mid - 1;
     }
-    const FwdArgs<T> a = args[lo];
-    const int li = item - item_prefix[lo];
+    const FwdArgs<T> a = s_args[lo];
+    const int li = item - s_prefix[lo];
     ps.tmap = a.tmX;  // each surface's descriptor lives in device memory
     if constexpr (PIPE == 0) {
       process_item_direct<T, TK, NW>(a, li, reinterpret_cast<T *>(smem_raw), st);
@@ -1107,6 +1104,9 @@ __device__ __forceinline__ void forward_batch_cta(const FwdArgs<T> *args, const 
         if ((threadIdx.x & 31) == 0) {
           const Item<T, 1> it(a, li, 0);
           produce_item<T, TK, NW>(a, it, ps, step);
+          // every copy of this item is issued: claim the next item while the
+          // consumers finish this one
+          s_item = atomicAdd(counter, 1);
         }
       } else {
         const Item<T, NW> it(a, li, w);
@@ -1119,13 +1119,14 @@ __device__ __forceinline__ void forward_batch_cta(const FwdArgs<T> *args, const 
         }
       }
     }
+    if (PIPE != 1 && threadIdx.x == 0) s_item = atomicAdd(counter, 1);
   }
   if constexpr (PIPE == 1) {
-    if (w == NW && (threadIdx.x & 31) == 0) drain_copies(ps, step, args[0].err);
+    if (w == NW && (threadIdx.x & 31) == 0) drain_copies(ps, step, args_g[0].err);
   }
   if constexpr (PIPE == 2) {
     __syncthreads();
-    if (threadIdx.x == 0 && abort_flag) drain_copies(ps, (unsigned)issued, args[0].err);
+    if (threadIdx.x == 0 && abort_flag) drain_copies(ps, (unsigned)issued, args_g[0].err);
   }
 }
 

@@ -102,6 +102,9 @@ struct FwdArgs {
   int withhold;         // testing: the copy pipeline issues no copies (every wait runs out)
 };
 
+// Surfaces in one batched call (their arguments sit in each CTA's shared memory).
+constexpr int kMaxBatchSurf = 32;
+
 template <typename T>
 struct AdjArgs {
   const T *coef;        // [P][O][16]
