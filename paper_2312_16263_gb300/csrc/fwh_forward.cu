@@ -550,8 +550,13 @@ __device__ __forceinline__ void consume_item(const FwdArgs<T> &a, const Item<T, 
 // x_k[2c+1], x_k+1[2c+1]), k = 64 b + 2 r: one swizzled row read per lane
 // gives both samples' series.  Lane l owns pair rows l + 32 t of a chunk
 // (samples s = 64 t + 2 l and s + 1) and forms, per observer, G = sum_q c_q
-// X_q and M likewise on the moments, all as scalar FMAs (a packed
-// fma.rn.f32x2 takes two issue cycles, so it buys no throughput over FFMA).
+// X_q and M likewise on the moments for both samples at once: (x_k[q],
+// x_k+1[q]) is a register pair, and packed fma.rn.f32x2 with c_q in both
+// halves computes the two samples' dot products.  A packed FMA issues in one
+// slot and occupies the FMA pipe for two cycles, so the 16 multiply-adds of
+// the two dot products take 8 issue slots instead of 16: the kernel is bound
+// by instruction issue, not by the FMA pipe.  Results are those of scalar
+// fmaf (both round each element to nearest).
 // Sample s adds a G + cc M (left spline node) to window slot 1 + s + off and
 // b G + dd M (right node) to slot s + off, so slot 1 + s + off receives
 // a G_s + cc M_s + b G_s+1 + dd M_s+1.  For the first sample of a pair both
@@ -729,6 +734,32 @@ __device__ __forceinline__ void sts_f32x2(unsigned addr, float2 v) {
   asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
 
+// Packed FP32 pairs (fma.rn.f32x2 and friends): element-wise IEEE round-to-
+// nearest operations on two floats held in a 64-bit register pair.  One
+// packed FMA issues in one slot and keeps the FMA pipe busy for two cycles.
+using f32x2 = unsigned long long;
+__device__ __forceinline__ void lds_v2f32x2(unsigned addr, f32x2 &a, f32x2 &b) {
+  asm("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
+}
+__device__ __forceinline__ f32x2 f2_dup(float x) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ void f2_split(f32x2 v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
 template <int TK, int NW, bool PF, int PIPE, bool KAHAN>
 __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
                                                  const Item<float, NW> &it,
@@ -748,8 +779,10 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
   const unsigned win_s = smem_u32(wwin) + (unsigned)lane * EB;
   const unsigned stage0 = smem_u32(ps.stage0);
   // X pair row r = lane + 32 t of a stage: 16-byte chunk c at c ^ (lane & 7).
-  const unsigned xrow = (unsigned)lane * 128u;
-  const unsigned xswz = ((unsigned)lane & 7u) << 4;
+  // Stages are 1024-byte aligned and a pair row is 128 bytes, so bits 4..6 of
+  // (stage + 128 lane) are zero and chunk c of the lane's row sits at
+  // (stage + 128 lane + 16 (lane & 7)) ^ 16 c: one XOR per chunk.
+  const unsigned xrow = (unsigned)lane * 128u + (((unsigned)lane & 7u) << 4);
   const bool first = lane == 0;
   unsigned s = step % (unsigned)ps.nst, ph = (step / (unsigned)ps.nst) & 1u;
   const int nsteps = (it.p_end - it.p_begin) * ((it.k_end - it.k_begin) / CH);
@@ -758,17 +791,15 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
     for (int p = it.p_begin; p < it.p_end; ++p, ++step, ++j) {
       if (!mbar_wait(&ps.full[s], ph, a.err, ps.abort, a.wait_cycles)) return;
       const unsigned stg = stage_token(stage0 + s * ps.stage_bytes);
-      float X[NP][2][kRec];  // [pair row][sample 2r, 2r + 1][value]
+      // XP[t][q] = (value q of sample 2r, value q of sample 2r + 1): the 16-byte
+      // chunk c holds the pairs of values 2c and 2c + 1
+      f32x2 XP[NP][kRec];
+      const unsigned xb = stg + xrow;
 #pragma unroll
       for (int t = 0; t < NP; ++t) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const float4 v = lds_v4f32(stg + xrow + 4096u * t + (((unsigned)c << 4) ^ xswz));
-          X[t][0][2 * c] = v.x;
-          X[t][1][2 * c] = v.y;
-          X[t][0][2 * c + 1] = v.z;
-          X[t][1][2 * c + 1] = v.w;
-        }
+        for (int c = 0; c < 8; ++c)
+          lds_v2f32x2((xb ^ ((unsigned)c << 4)) + 4096u * t, XP[t][2 * c], XP[t][2 * c + 1]);
       }
       const unsigned crec = stg + ps.x_bytes + (unsigned)w * RB;
       // window base of this panel's updates, ordered after the previous
@@ -778,6 +809,29 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
       auto observer = [&](int m, const Coef &k) {
         const unsigned base = wtok + (unsigned)m * win_b;
         const unsigned A0 = base + k.r0, A1 = base + k.r1;
+        // signal G and moment M of both samples of each pair row: packed dot
+        // products c . X with the coefficient in both halves of a register
+        // pair (issued after the window loads, which then hide their latency)
+        f32x2 Gp[NP], Mp[NP];
+        auto dots = [&]() {
+          {
+            const f32x2 cp = f2_dup(k.c[0]);
+#pragma unroll
+            for (int t = 0; t < NP; ++t) {
+              Gp[t] = f2_mul(cp, XP[t][0]);
+              Mp[t] = f2_mul(cp, XP[t][8]);
+            }
+          }
+#pragma unroll
+          for (int q = 1; q < 8; ++q) {
+            const f32x2 cp = f2_dup(k.c[q]);
+#pragma unroll
+            for (int t = 0; t < NP; ++t) {
+              Gp[t] = f2_fma(cp, XP[t][q], Gp[t]);
+              Mp[t] = f2_fma(cp, XP[t][8 + q], Mp[t]);
+            }
+          }
+        };
         if constexpr (!KAHAN) {
           float s0[NP], s1[NP], v0[NP];
 #pragma unroll
@@ -789,17 +843,12 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
           // lane below, in the window, and discard it); no lane stores to it
           // before lane 0 does, so it is read early to hide the latency
           const float e_old = lds_win(A1 - 4u);
+          dots();
 #pragma unroll
           for (int t = 0; t < NP; ++t) {
-            float G0 = k.c[0] * X[t][0][0], M0 = k.c[0] * X[t][0][8];
-            float G1 = k.c[0] * X[t][1][0], M1 = k.c[0] * X[t][1][8];
-#pragma unroll
-            for (int q = 1; q < 8; ++q) {
-              G0 = fmaf(k.c[q], X[t][0][q], G0);
-              M0 = fmaf(k.c[q], X[t][0][8 + q], M0);
-              G1 = fmaf(k.c[q], X[t][1][q], G1);
-              M1 = fmaf(k.c[q], X[t][1][8 + q], M1);
-            }
+            float G0, G1, M0, M1;
+            f2_split(Gp[t], G0, G1);
+            f2_split(Mp[t], M0, M1);
             // slot of the pair's first sample: both spline nodes are this lane's
             s0[t] = fmaf(k.wdd, M1, fmaf(k.wb, G1, fmaf(k.wcc, M0, fmaf(k.wa, G0, s0[t]))));
             // slot of the second: its left node, the right one comes from above
@@ -831,18 +880,13 @@ __device__ __forceinline__ void consume_item_f32(const FwdArgs<float> &a,
             w1[t] = lds_win2(A1 + 256u * t);
           }
           const float2 e_old = lds_win2(A1 - 8u);
+          dots();
           float y0[NP], y1[NP], v0[NP];
 #pragma unroll
           for (int t = 0; t < NP; ++t) {
-            float G0 = k.c[0] * X[t][0][0], M0 = k.c[0] * X[t][0][8];
-            float G1 = k.c[0] * X[t][1][0], M1 = k.c[0] * X[t][1][8];
-#pragma unroll
-            for (int q = 1; q < 8; ++q) {
-              G0 = fmaf(k.c[q], X[t][0][q], G0);
-              M0 = fmaf(k.c[q], X[t][0][8 + q], M0);
-              G1 = fmaf(k.c[q], X[t][1][q], G1);
-              M1 = fmaf(k.c[q], X[t][1][8 + q], M1);
-            }
+            float G0, G1, M0, M1;
+            f2_split(Gp[t], G0, G1);
+            f2_split(Mp[t], M0, M1);
             y0[t] = fmaf(k.wdd, M1, fmaf(k.wb, G1, fmaf(k.wcc, M0, k.wa * G0)));
             y1[t] = fmaf(k.wcc, M1, k.wa * G1);
             v0[t] = fmaf(k.wdd, M0, k.wb * G0);
@@ -1081,7 +1125,9 @@ __device__ __forceinline__ void forward_batch_cta(const FwdArgs<T> *args_g,
       const int mid = (lo + hi + 1) >> 1;
       if (s_prefix[mid] <= item) lo = mid; else hi = mid - 1;
     }
-    const FwdArgs<T> a = s_args[lo];
+    // a reference, not a copy: the fields are read from shared memory where
+    // used, instead of holding the whole argument block in registers
+    const FwdArgs<T> &a = s_args[lo];
     const int li = item - s_prefix[lo];
     ps.tmap = a.tmX;  // each surface's descriptor lives in device memory
     if constexpr (PIPE == 0) {
@@ -1146,10 +1192,11 @@ __global__ void __maxnreg__(200)
 
 // Candidate tile shapes {pipe, tk, warps, obs_per_warp, win, seg_chunks,
 // stages, acc, wide}.  acc: 0 one sample per lane per block (FP64), 3 a pair
-// of consecutive samples per lane per block with split windows (FP32; its
-// series rows pair those samples, so every FP32 shape is a TMA shape), 4 the
-// same with the next observer's record read ahead.  wide: register cap 200
-// instead of the launch bounds' occupancy target.
+// of consecutive samples per lane per block with split windows and packed
+// dot products (FP32; its series rows pair those samples, so every FP32 shape
+// is a TMA shape), 4 the same with the next observer's record read ahead, 5
+// as 4 with compensated (Kahan) window sums.  wide: register cap 200 instead
+// of the launch bounds' occupancy target.
 constexpr FwdConfig kCfgF32[] = {
     {1, 4, 4, 9, 224, 4, 3, 4, 0},
     {1, 4, 4, 9, 224, 2, 3, 4, 0},
