@@ -298,8 +298,8 @@ def extra_legs(dev):
     """Workloads 1 (plain FP64), 3 (mixed and FP64), 4 (backward), 5 (eight
     surfaces, batched) and the PSD of workload 2's signals, each timed with
     CUDA events on inputs resident in HBM, with the error against the oracle on
-    a sample of observers and the oracle's rate on this host (SURVEY-style
-    side-by-side).  Returns a dict of keys for the JSON line."""
+    a sample of observers and the oracle's rate on this host beside it.
+    Returns a dict of keys for the JSON line."""
     import numpy as np
     import torch
     from fwh_inputs import batch_workloads, workload
@@ -369,9 +369,11 @@ def extra_legs(dev):
     out["backward"] = leg
     del f, g_p
     torch.cuda.empty_cache()
-    # workload 5: eight uneven surfaces, one graph of per-segment persistent
-    # launches with the series streamed through a two-segment ring, against
-    # one fwh_forward call per surface; the smallest surface against the oracle
+    # workload 5: eight uneven surfaces in one graph-captured call (whole
+    # records, pipelined form), one fwh_forward call per surface, the single
+    # grid and persistent forms, and the series streamed through a ring of two
+    # 512-sample segments per surface (four rounds); the smallest surface
+    # against the oracle
     ws5 = batch_workloads()
     surfs = [FWH.from_workload(x, "mixed") for x in ws5]
     fields = [x.fields(device=dev, dtype="float32") for x in ws5]
@@ -387,15 +389,47 @@ def extra_legs(dev):
     err_b = rel_l2_stats(outs[small].cpu().numpy(), nv, p_ref, nv_ref, pick)
     ms_s = _time_calls(lambda: [sx.forward(fx, ox) for sx, fx, ox in zip(surfs, fields, outs)],
                        2, warm=1)
-    free_s = torch.cuda.mem_get_info()[0]
+    # the other launch forms over the same items: one grid, the persistent
+    # work-queue kernel
+    ms_f, err_f = {}, {}
+    for form in ("grid", "persistent"):
+        surfs[0].set_batch_options(0, form)
+        outs_p = batch_forward(surfs, fields)
+        ms_f[form] = _time_calls(lambda: batch_forward(surfs, fields, outs_p), 3, warm=1)
+        surfs[0].check()
+        err_f[form] = rel_l2_stats(outs_p[small].cpu().numpy(), nv, p_ref, nv_ref, pick)
+        del outs_p
+    # the ring: series of 1024 samples per surface instead of 4096 (the
+    # handles' whole-record buffers are released first, so the free memory
+    # below is what a streamed call needs)
+    for sx in surfs:
+        sx.close()
+    surfs = [FWH.from_workload(x, "mixed") for x in ws5]
+    surfs[0].set_batch_options(1024, "pipelined")
+    outs_r = batch_forward(surfs, fields)
+    ms_r = _time_calls(lambda: batch_forward(surfs, fields, outs_r), 3, warm=1)
+    surfs[0].check()
+    free_r = torch.cuda.mem_get_info()[0]
+    err_r = rel_l2_stats(outs_r[small].cpu().numpy(), nv, p_ref, nv_ref, pick)
     out["batch"] = {"workload": "eight surfaces, 524288 panels x 4096 steps x 1024 observers each",
                     "evals": ev5, "ms": ms_b, "evals_per_s": ev5 / (ms_b / 1e3),
+                    "form": "pipelined: whole records, one launch per surface, each "
+                            "surface's prep under the scatters before it",
                     "per_surface_calls_ms": ms_s, "per_surface_evals_per_s": ev5 / (ms_s / 1e3),
-                    "device_free_gb_batched": free_b / 1e9,
-                    "device_free_gb_after_per_surface_calls": free_s / 1e9,
-                    "mixed_vs_oracle_rel_l2": err_b, "oracle_evals_per_s": orate,
+                    "grid_ms": ms_f["grid"], "grid_evals_per_s": ev5 / (ms_f["grid"] / 1e3),
+                    "persistent_ms": ms_f["persistent"],
+                    "persistent_evals_per_s": ev5 / (ms_f["persistent"] / 1e3),
+                    "grid_vs_oracle_rel_l2": err_f["grid"],
+                    "persistent_vs_oracle_rel_l2": err_f["persistent"],
+                    "streamed_ms": ms_r, "streamed_evals_per_s": ev5 / (ms_r / 1e3),
+                    "streamed_form": "pipelined, ring of 2 x 512 samples per surface, 4 rounds",
+                    "device_free_gb_whole_records": free_b / 1e9,
+                    "device_free_gb_streamed": free_r / 1e9,
+                    "mixed_vs_oracle_rel_l2": err_b, "streamed_vs_oracle_rel_l2": err_r,
+                    "oracle_evals_per_s": orate,
                     "oracle_sample": f"surface {small} ({ws5[small].surface.n_panels} panels), "
                                      "2 observers"}
+    del outs_r
     for sx in surfs:
         sx.close()
     del surfs, fields, outs

@@ -66,6 +66,8 @@ typedef enum {
 } fwh_status;
 
 enum { FWH_FP64 = 0, FWH_MIXED = 1 };
+/* launch forms of batched calls (fwh_set_batch_options) */
+enum { FWH_BATCH_PIPELINED = 0, FWH_BATCH_GRID = 1, FWH_BATCH_PERSISTENT = 2 };
 
 /*
  * Create a handle for one permeable surface of n_panels subfaces
@@ -154,21 +156,42 @@ fwh_status fwh_backward(fwh_handle h, const void *fields, int64_t nt,
 
 /*
  * Batched forward over n handles (several uneven surfaces, each with its own
- * observers, fields, nt and p_out); all handles must share one precision and
- * take device buffers.  Source time is streamed in segments (512 samples
- * under the default tile shape): per segment, the series of every surface are
- * prepared on a high-priority stream, then one persistent work-queue kernel
- * scatters the work items of every surface in that segment, while the next
- * segment is being prepared.  A surface whose record spans more than two
- * segments keeps only a ring of two segments of series (P x 1024 rows instead
- * of P x round_up(nt, 256)).  The whole sequence is captured once in a CUDA
- * graph keyed on the handle set and replayed on later calls with the same
- * arguments.
- * Errors: FWH_ERR_ARG (n < 1, mixed precisions, null entries),
+ * observers, fields, nt and p_out; the surface sum of Sec. III C over the
+ * Faces of Sec. III A); all handles must share one precision and take device
+ * buffers.  By default the series of every surface are kept for the whole
+ * record.  With a ring set on hs[0] (fwh_set_batch_options), the record is
+ * streamed instead in rounds of R time segments (512 samples each under the
+ * default tile shape): each surface keeps the series of R segments only
+ * (P x 512 R rows instead of P x round_up(nt, 256)).  The work items (panel
+ * set x time segment x observer group) are scattered in the launch form set
+ * on hs[0]: FWH_BATCH_PIPELINED (default) one launch per surface and round,
+ * each surface's series prepared on a high-priority stream while the
+ * surfaces before it scatter; FWH_BATCH_GRID one grid per round over every
+ * surface's items; FWH_BATCH_PERSISTENT one persistent work-queue kernel per
+ * round.  The whole sequence is captured once in a CUDA graph keyed on the
+ * handle set and the options, and replayed on later calls with the same
+ * arguments.  At most 32 surfaces.
+ * Errors: FWH_ERR_ARG (n < 1 or > 32, mixed precisions, null entries),
  * FWH_ERR_STATE (a handle without observers), FWH_ERR_CUDA.
  */
 fwh_status fwh_batch_forward(int n, const fwh_handle *hs, const void *const *fields,
                              const int64_t *nt, double *const *p_out, void *stream);
+
+/*
+ * Options of batched calls led by h (h = hs[0] of fwh_batch_forward).
+ * ring_samples = 0 (the default) keeps every surface's series for its whole
+ * record; ring_samples > 0 streams records longer than that through a ring
+ * of max(1, floor(ring_samples / 512)) time segments of 512 samples (default
+ * tile shape), 64 bytes (FP32) or 128 bytes (FP64) per panel and sample.
+ * form: FWH_BATCH_PIPELINED, FWH_BATCH_GRID or FWH_BATCH_PERSISTENT (see
+ * fwh_batch_forward).  On a GB300 the pipelined form is the fastest; the
+ * single grid reads its per-surface arguments from a parameter block by
+ * surface index (about 1 % slower per item), and the persistent kernel keeps
+ * each CTA's warps on the same schedulers for the whole launch (about 3 %).
+ * Results agree to the FP64 rounding of the output sums.
+ * Errors: FWH_ERR_ARG for a negative ring length or an unknown form.
+ */
+fwh_status fwh_set_batch_options(fwh_handle h, int64_t ring_samples, int form);
 
 /*
  * Pipelined forward passes (default off): with device fields and a record of

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libfwh_gb300.so")
 
 FWH_OK, FWH_ERR_ARG, FWH_ERR_CUDA, FWH_ERR_OOM, FWH_ERR_STATE, FWH_ERR_TIMEOUT = range(6)
 FWH_FP64, FWH_MIXED = 0, 1
+FWH_BATCH_PIPELINED, FWH_BATCH_GRID, FWH_BATCH_PERSISTENT = 0, 1, 2
 STATUS_NAMES = {0: "FWH_OK", 1: "FWH_ERR_ARG", 2: "FWH_ERR_CUDA", 3: "FWH_ERR_OOM",
                 4: "FWH_ERR_STATE", 5: "FWH_ERR_TIMEOUT"}
 
@@ -41,6 +42,7 @@ SIGNATURES = {
     "fwh_set_tile_config": (ctypes.c_int, [_vp, ctypes.c_int]),
     "fwh_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "fwh_set_pipeline": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "fwh_set_batch_options": (ctypes.c_int, [_vp, _i64, ctypes.c_int]),
     "fwh_set_wait_limit": (ctypes.c_int, [_vp, _i64, ctypes.c_int]),
     "fwh_last_timings": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)]),
     "fwh_timing_totals": (ctypes.c_int, [_vp, _dp, _ip64, ctypes.c_int]),

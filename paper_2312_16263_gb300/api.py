@@ -155,6 +155,16 @@ class FWH:
         """Overlap the series prep of later time segments with the scatter."""
         _abi.check(self.lib.fwh_set_pipeline(self.h, int(bool(enable))), self.h)
 
+    def set_batch_options(self, ring: int = 0, form: str = "pipelined"):
+        """Options of batched calls this surface leads (first in the list):
+        ring = 0 keeps whole records, > 0 streams them through a ring of that
+        many source samples (whole 512-sample segments, at least one); form
+        is "pipelined" (one launch per surface, preps overlapped), "grid" (one
+        grid over every surface) or "persistent" (the work-queue kernel)."""
+        forms = {"pipelined": _abi.FWH_BATCH_PIPELINED, "grid": _abi.FWH_BATCH_GRID,
+                 "persistent": _abi.FWH_BATCH_PERSISTENT}
+        _abi.check(self.lib.fwh_set_batch_options(self.h, int(ring), forms[form]), self.h)
+
     def set_timing(self, enable: bool = True):
         _abi.check(self.lib.fwh_set_timing(self.h, int(bool(enable))), self.h)
 
@@ -233,7 +243,8 @@ def moving_forward(y: torch.Tensor, normals: torch.Tensor, velocities: torch.Ten
 
 def batch_forward(surfaces: Sequence[FWH], fields: Sequence[torch.Tensor],
                   outs: Sequence[torch.Tensor] | None = None, stream=None):
-    """One persistent, graph-captured launch over several surfaces."""
+    """Several surfaces in one graph-captured call (launch form and series
+    ring set on surfaces[0] with set_batch_options)."""
     n = len(surfaces)
     if outs is None:
         outs = [torch.empty((s.O, f.shape[0]), dtype=torch.float64, device=f.device)

@@ -40,19 +40,21 @@ struct Graph {
   std::vector<uintptr_t> key;
 };
 
-// Device-side argument table of one batched launch (lives with its graph).
-// Device-side argument tables of one batched call (live with its graph): per
-// time segment q, the FwdArgs of every surface and the prefix sums of their
-// work items.
+// Plan of one batched call (lives with its graph): per round r (a run of
+// consecutive time segments whose series are resident together), the launch
+// parameters (every surface's FwdArgs, X descriptor and first work item).
 struct BatchPlan {
-  Buf args, prefix, counter;   // [nq][n] FwdArgs, [nq][n + 1] ints, [nq] ints
-  Buf tmaps;                   // [n] X tensor maps (128 bytes each)
-  std::vector<int> total;      // work items of each segment's persistent launch
+  Buf counter;                 // [nr] work-queue counters
+  std::vector<BatchParams<float>> pf;   // [nr] launch parameters (FP32 surfaces)
+  std::vector<BatchParams<double>> pd;  // [nr] launch parameters (FP64 surfaces)
+  std::vector<int> total;      // work items of each round's scatter launch
   std::vector<int> x_ld;       // X rows per panel of each surface (ring or whole record)
   std::vector<int> nseg;       // time segments of each surface
-  int nq = 0, ctas = 0, cfg = 0, seg = 0;
+  int nq = 0;                  // time segments of the longest record
+  int R = 0;                   // segments per round (nq: the whole record in one round)
+  int nr = 0, ctas = 0, cfg = 0, seg = 0;
+  int form = FWH_BATCH_PIPELINED;  // launch form (fwh_set_batch_options)
 };
-constexpr int kRingSegs = 2;   // time segments of X a batched call keeps per surface
 
 }  // namespace
 
@@ -80,6 +82,9 @@ struct fwh_ctx {
   long long wait_limit = 0;      // bound of the forward pipeline waits (0: default)
   int withhold = 0;              // testing: the forward pipeline issues no copies
   bool pipeline = false;         // device fields: prep of later segments overlaps the scatter
+  int64_t batch_ring = 0;        // batched calls led by this handle: source samples of
+                                 // series kept per surface (0: the whole record)
+  int batch_form = FWH_BATCH_PIPELINED;  // ... and their launch form
   // deferred device check: each call with device outputs copies the error flag
   // into pinned host memory; the next call (or fwh_check) reads it
   int *h_err = nullptr;
@@ -109,6 +114,7 @@ struct fwh_ctx {
   cudaStream_t side = nullptr;
   cudaStream_t copy = nullptr;              // host-field slabs (fwh_forward)
   cudaStream_t pstream = nullptr;           // their series prep
+  cudaStream_t bstream = nullptr;           // second scatter lane of pipelined batches
   std::vector<cudaEvent_t> slab_ev;         // per slab: copied, prepared; plus the start
   cudaEvent_t bev[2] = {nullptr, nullptr};
 };
@@ -524,12 +530,7 @@ void drop_graphs(fwh_handle h) {
   for (auto &kv : h->graphs)
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   h->graphs.clear();
-  for (auto &kv : h->bplans) {
-    release(kv.second.args);
-    release(kv.second.prefix);
-    release(kv.second.counter);
-    release(kv.second.tmaps);
-  }
+  for (auto &kv : h->bplans) release(kv.second.counter);
   h->bplans.clear();
 }
 
@@ -1056,6 +1057,16 @@ fwh_status fwh_set_pipeline(fwh_handle h, int enable) {
   return FWH_OK;
 }
 
+fwh_status fwh_set_batch_options(fwh_handle h, int64_t ring_samples, int form) {
+  if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
+  if (ring_samples < 0) return fail(h, FWH_ERR_ARG, "ring length must be >= 0 samples");
+  if (form != FWH_BATCH_PIPELINED && form != FWH_BATCH_GRID && form != FWH_BATCH_PERSISTENT)
+    return fail(h, FWH_ERR_ARG, "unknown batched launch form");
+  h->batch_ring = ring_samples;
+  h->batch_form = form;
+  return FWH_OK;
+}
+
 fwh_status fwh_set_timing(fwh_handle h, int enable) {
   if (!h) return fail(nullptr, FWH_ERR_ARG, "handle is NULL");
   h->timing = enable != 0;
@@ -1095,12 +1106,7 @@ void fwh_destroy(fwh_handle h) {
   if (!h) return;
   for (auto &kv : h->graphs)
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-  for (auto &kv : h->bplans) {
-    release(kv.second.args);
-    release(kv.second.prefix);
-    release(kv.second.counter);
-    release(kv.second.tmaps);
-  }
+  for (auto &kv : h->bplans) release(kv.second.counter);
   for (double *p : {h->d_y, h->d_n, h->d_dS, h->d_x, h->d_Rmax, h->d_Rmin})
     if (p) cudaFree(p);
   if (h->d_perm) cudaFree(h->d_perm);
@@ -1119,6 +1125,7 @@ void fwh_destroy(fwh_handle h) {
   if (h->side) cudaStreamDestroy(h->side);
   if (h->copy) cudaStreamDestroy(h->copy);
   if (h->pstream) cudaStreamDestroy(h->pstream);
+  if (h->bstream) cudaStreamDestroy(h->bstream);
   for (cudaEvent_t e : h->slab_ev) cudaEventDestroy(e);
   delete h;
 }
@@ -1126,11 +1133,20 @@ void fwh_destroy(fwh_handle h) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Batched forward: several surfaces, one persistent work-queue launch.
-// Host-side planning and the upload of the per-surface argument table happen
-// once per argument set; the device work (output clears, integrand prep of
-// every surface, queue reset, persistent scatter) is captured in a CUDA graph
-// and replayed.
+// Batched forward: several surfaces in one graph-captured call.
+// Host-side planning (the launch parameter blocks) happens once per argument
+// set; the device work (output clears, integrand prep of every surface,
+// scatter launches) is captured in a CUDA graph and replayed.
+//
+// The record is cut into rounds of R consecutive time segments.  By default
+// one round holds the whole record: the series of every surface are prepared
+// first and ONE launch scatters every work item of every surface.  With a
+// ring (fwh_set_batch_options), X keeps R segments per surface and the rounds
+// alternate prep and scatter.  Within a round the work items run in the order
+// (surface, panel set, segment, observer group), so the CTAs in flight at any
+// moment share a few panel sets' coefficient records and X rows in L2.  The
+// scatter launch is one grid with a CTA per item (default) or the persistent
+// work-queue kernel with one CTA per SM slot.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -1145,10 +1161,22 @@ int batch_cfg(int n, const fwh_handle *hs, fwh_handle h0) {
   return cfg;
 }
 
-// X rows per panel of a surface in a batched call: records longer than
-// kRingSegs time segments stream through a ring of kRingSegs segments.
-int batch_x_ld(const fwh_ctx *h, int seg) {
-  return (h->ntp + seg - 1) / seg > kRingSegs ? kRingSegs * seg : h->ntp;
+template <typename T> std::vector<BatchParams<T>> &batch_params(BatchPlan &bp);
+template <> std::vector<BatchParams<float>> &batch_params<float>(BatchPlan &bp) { return bp.pf; }
+template <> std::vector<BatchParams<double>> &batch_params<double>(BatchPlan &bp) { return bp.pd; }
+template <typename T> const std::vector<BatchParams<T>> &batch_params(const BatchPlan &bp) {
+  return batch_params<T>(const_cast<BatchPlan &>(bp));
+}
+
+// Segments per round of a batched call led by h0 (0: the whole record).
+int batch_round_segs(const fwh_ctx *h0, int seg) {
+  return h0->batch_ring > 0 ? (int)std::max<int64_t>(1, h0->batch_ring / seg) : 0;
+}
+
+// X rows per panel of a surface in a batched call: the whole record, or a
+// ring of R time segments when the record spans more than R of them.
+int batch_x_ld(const fwh_ctx *h, int seg, int R) {
+  return R > 0 && (h->ntp + seg - 1) / seg > R ? R * seg : h->ntp;
 }
 
 template <typename T>
@@ -1158,28 +1186,29 @@ fwh_status batch_build(int n, const fwh_handle *hs, double *const *p_out, fwh_ha
   const int cfg = batch_cfg(n, hs, h0);
   const FwdConfig c = fwd_config(fp64, cfg);
   const int seg = c.seg_chunks * 32 * c.tk;
+  const int R0 = batch_round_segs(h0, seg);
   std::vector<FwdArgs<T>> base(n);
-  std::vector<unsigned char> maps((size_t)n * 128, 0);
+  std::vector<TmapBytes> maps(n);
   bp.x_ld.assign(n, 0);
   bp.nseg.assign(n, 0);
   bp.nq = 0;
-  CK(h0, ensure(bp.tmaps, (size_t)n * 128));
   for (int i = 0; i < n; ++i) {
     fwh_handle h = hs[i];
     fwh_status st = plan(h, c, h0->side);
     if (st != FWH_OK) return fail(h0, st, h->err);
     CK(h0, cudaStreamSynchronize(h0->side));
     bp.nseg[i] = (h->ntp + seg - 1) / seg;
-    bp.x_ld[i] = batch_x_ld(h, seg);
+    bp.x_ld[i] = batch_x_ld(h, seg, R0);
     bp.nq = std::max(bp.nq, bp.nseg[i]);
     if (h->X.bytes < (size_t)h->P * bp.x_ld[i] * kRec * sizeof(T))
       return fail(h0, FWH_ERR_STATE, "series buffer of a batched surface is too small");
+    std::memset(maps[i].b, 0, sizeof maps[i].b);
     if (c.pipe != 0 &&
-        !encode_x_tensor_map(maps.data() + (size_t)i * 128, h->X.p,
-                             (unsigned long long)h->P * bp.x_ld[i], fp64, 32 * c.tk))
+        !encode_x_tensor_map(maps[i].b, h->X.p, (unsigned long long)h->P * bp.x_ld[i], fp64,
+                             32 * c.tk))
       return fail(h0, FWH_ERR_CUDA, "cuTensorMapEncodeTiled refused the series layout");
     FwdArgs<T> &fa = base[i];
-    fa.tmX = static_cast<unsigned char *>(bp.tmaps.p) + (size_t)i * 128;
+    fa.tmX = nullptr;  // the launch passes the descriptors in its parameter block
     fa.wait_cycles = h0->wait_limit;
     fa.withhold = h0->withhold;
     fa.X = reinterpret_cast<const T *>(h->X.p);
@@ -1201,32 +1230,33 @@ fwh_status batch_build(int n, const fwh_handle *hs, double *const *p_out, fwh_ha
     fa.win = c.win;
     fa.wfl = c.win * (c.acc == 5 ? 2 : 1);
   }
-  // one persistent launch per time segment over every surface's items of it
-  std::vector<FwdArgs<T>> args((size_t)bp.nq * n);
-  std::vector<int> prefix((size_t)bp.nq * (n + 1), 0);
-  bp.total.assign(bp.nq, 0);
-  for (int q = 0; q < bp.nq; ++q) {
+  // one scatter launch per round over every surface's items of it
+  bp.R = R0 > 0 ? std::min(R0, bp.nq) : bp.nq;
+  bp.nr = (bp.nq + bp.R - 1) / bp.R;
+  std::vector<BatchParams<T>> &prm = batch_params<T>(bp);
+  prm.assign(bp.nr, BatchParams<T>{});
+  bp.total.assign(bp.nr, 0);
+  for (int r = 0; r < bp.nr; ++r) {
+    BatchParams<T> &P = prm[r];
+    P.n_surf = n;
+    P.prefix[0] = 0;
     for (int i = 0; i < n; ++i) {
       FwdArgs<T> fa = base[i];
-      const bool has = q < bp.nseg[i];
-      fa.seg_lo = has ? q : 0;
-      fa.seg_cnt = 1;
-      args[(size_t)q * n + i] = fa;
-      prefix[(size_t)q * (n + 1) + i + 1] =
-          prefix[(size_t)q * (n + 1) + i] + (has ? fa.nsets * fa.n_obs_groups : 0);
+      const int cnt = std::min(bp.nseg[i], (r + 1) * bp.R) - r * bp.R;
+      const bool has = cnt > 0;
+      fa.seg_lo = has ? r * bp.R : 0;
+      fa.seg_cnt = has ? cnt : 1;
+      P.a[i] = fa;
+      P.tm[i] = maps[i];
+      P.prefix[i + 1] = P.prefix[i] + (has ? fa.nsets * fa.n_obs_groups * cnt : 0);
     }
-    bp.total[q] = prefix[(size_t)q * (n + 1) + n];
+    P.total = P.prefix[n];
+    bp.total[r] = P.total;
   }
   bp.seg = seg;
   bp.cfg = cfg;
-  CK(h0, cudaMemcpy(bp.tmaps.p, maps.data(), maps.size(), cudaMemcpyHostToDevice));
-  CK(h0, ensure(bp.args, args.size() * sizeof(FwdArgs<T>)));
-  CK(h0, ensure(bp.prefix, prefix.size() * sizeof(int)));
-  CK(h0, ensure(bp.counter, (size_t)bp.nq * sizeof(int)));
-  CK(h0, cudaMemcpy(bp.args.p, args.data(), args.size() * sizeof(FwdArgs<T>),
-                    cudaMemcpyHostToDevice));
-  CK(h0, cudaMemcpy(bp.prefix.p, prefix.data(), prefix.size() * sizeof(int),
-                    cudaMemcpyHostToDevice));
+  bp.form = h0->batch_form;
+  CK(h0, ensure(bp.counter, (size_t)bp.nr * sizeof(int)));
   int dev = 0, sms = 0;
   CK(h0, cudaGetDevice(&dev));
   CK(h0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1236,13 +1266,37 @@ fwh_status batch_build(int n, const fwh_handle *hs, double *const *p_out, fwh_ha
   return FWH_OK;
 }
 
-// The batched call's device work, enqueued on `s` (captured into a graph):
-// per time segment q, the series prep of every surface on the prep stream
-// (high priority), then one persistent scatter over all surfaces' items of
-// segment q on `s`.  The prep of segment q + 1 runs under the scatter of q;
-// with a ring, the prep of q waits for the scatter of q - kRingSegs, whose
-// rows it overwrites.
-constexpr int kBatchEv = 64;  // ordering events reused cyclically
+// The batched call's device work, enqueued on `s` (captured into a graph).
+// Per round r: the series prep of every surface's segments of r and the
+// scatter of their items.  FWH_BATCH_GRID / FWH_BATCH_PERSISTENT: the preps
+// on `s`, then one launch over all surfaces' items; with a ring, the prep of
+// round r overwrites the rows the scatter of round r - 1 read, so the rounds
+// run strictly one after the other.  FWH_BATCH_PIPELINED: one scatter launch
+// per (round, surface), each after its own prep, which runs on the handle's
+// high-priority stream; the preps of the other surfaces overlap the scatters
+// before them (a prep whose ring rows are still being read waits for that
+// surface's scatter of the previous round).
+template <typename T>
+fwh_status batch_prep(const fwh_handle h, const void *field, const BatchPlan &bp, int i, int r,
+                      fwh_handle h0, cudaStream_t s) {
+  const int cps = bp.seg / 64;
+  PrepArgs<T> pa{};
+  pa.fields = reinterpret_cast<const T *>(field);
+  pa.perm = h->identity ? nullptr : h->d_perm;
+  pa.n = h->d_n;
+  pa.X = reinterpret_cast<T *>(h->X.p);
+  pa.P = (int)h->P;
+  pa.nt = (int)h->nt;
+  pa.ntp = h->ntp;
+  pa.x_ld = bp.x_ld[i];
+  pa.ca = h->ca;
+  pa.sa = h->sa;
+  pa.dt = h->dt;
+  pa.c_lo = r * bp.R * cps;
+  pa.c_hi = std::min(h->ntp / 64, (r + 1) * bp.R * cps);
+  CK(h0, launch_prep<T>(pa, s));
+  return FWH_OK;
+}
 
 template <typename T>
 fwh_status batch_enqueue(int n, const fwh_handle *hs, const void *const *fields,
@@ -1250,43 +1304,63 @@ fwh_status batch_enqueue(int n, const fwh_handle *hs, const void *const *fields,
                          cudaStream_t s) {
   for (int i = 0; i < n; ++i)
     CK(h0, cudaMemsetAsync(p_out[i], 0, (size_t)hs[i]->O * hs[i]->nt * sizeof(double), s));
-  CK(h0, cudaMemsetAsync(bp.counter.p, 0, (size_t)bp.nq * sizeof(int), s));
-  cudaEvent_t *ev = h0->slab_ev.data();  // [0]: fork, [1]: join, then prep and scatter rings
-  cudaEvent_t *ev_prep = ev + 2, *ev_scat = ev + 2 + kBatchEv;
+  CK(h0, cudaMemsetAsync(bp.counter.p, 0, (size_t)bp.nr * sizeof(int), s));
+  const std::vector<BatchParams<T>> &prm = batch_params<T>(bp);
+  if (bp.form != FWH_BATCH_PIPELINED) {
+    for (int r = 0; r < bp.nr; ++r) {
+      for (int i = 0; i < n; ++i) {
+        if (r * bp.R >= bp.nseg[i]) continue;
+        fwh_status st = batch_prep<T>(hs[i], fields[i], bp, i, r, h0, s);
+        if (st != FWH_OK) return st;
+      }
+      if (bp.total[r] == 0) continue;
+      if (bp.form == FWH_BATCH_PERSISTENT)
+        CK(h0, launch_forward_batch<T>(prm[r], reinterpret_cast<int *>(bp.counter.p) + r, bp.cfg,
+                                       std::min(bp.ctas, bp.total[r]), s));
+      else
+        CK(h0, launch_forward_multi<T>(prm[r], bp.cfg, s));
+    }
+    return FWH_OK;
+  }
+  fwh_status st = ensure_pstream(h0);
+  if (st == FWH_OK) st = ensure_events(h0, 2 + 2 * bp.nr * n);
+  if (st != FWH_OK) return st;
+  if (!h0->bstream) CK(h0, cudaStreamCreateWithFlags(&h0->bstream, cudaStreamNonBlocking));
+  cudaEvent_t *ev = h0->slab_ev.data();  // [0] fork, [1] join, prep and scatter events per (r, i)
+  cudaEvent_t *ev_prep = ev + 2, *ev_scat = ev + 2 + bp.nr * n;
   CK(h0, cudaEventRecord(ev[0], s));
   CK(h0, cudaStreamWaitEvent(h0->pstream, ev[0], 0));
-  const int cps = bp.seg / 64;
-  for (int q = 0; q < bp.nq; ++q) {
-    if (q >= kRingSegs) CK(h0, cudaStreamWaitEvent(h0->pstream, ev_scat[(q - kRingSegs) % kBatchEv], 0));
-    for (int i = 0; i < n; ++i) {
-      if (q >= bp.nseg[i]) continue;
-      fwh_handle h = hs[i];
-      PrepArgs<T> pa{};
-      pa.fields = reinterpret_cast<const T *>(fields[i]);
-      pa.perm = h->identity ? nullptr : h->d_perm;
-      pa.n = h->d_n;
-      pa.X = reinterpret_cast<T *>(h->X.p);
-      pa.P = (int)h->P;
-      pa.nt = (int)h->nt;
-      pa.ntp = h->ntp;
-      pa.x_ld = bp.x_ld[i];
-      pa.ca = h->ca;
-      pa.sa = h->sa;
-      pa.dt = h->dt;
-      pa.c_lo = q * cps;
-      pa.c_hi = std::min(h->ntp / 64, (q + 1) * cps);
-      CK(h0, launch_prep<T>(pa, h0->pstream));
+  CK(h0, cudaStreamWaitEvent(h0->bstream, ev[0], 0));
+  // surfaces in ascending size, so that only the smallest one's prep runs
+  // before any scatter; the scatters alternate between two streams, so one
+  // surface's tail overlaps the next surface's start
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return hs[x]->P * (int64_t)hs[x]->ntp < hs[y]->P * (int64_t)hs[y]->ntp;
+  });
+  cudaStream_t lane[2] = {s, h0->bstream};
+  int k = 0;
+  const bool ring = bp.nr > 1;
+  const FwdConfig c = fwd_config(sizeof(T) == 8, bp.cfg);
+  for (int r = 0; r < bp.nr; ++r) {
+    for (int i : order) {
+      if (r * bp.R >= bp.nseg[i]) continue;
+      if (ring && r > 0) CK(h0, cudaStreamWaitEvent(h0->pstream, ev_scat[(r - 1) * n + i], 0));
+      st = batch_prep<T>(hs[i], fields[i], bp, i, r, h0, h0->pstream);
+      if (st != FWH_OK) return st;
+      CK(h0, cudaEventRecord(ev_prep[r * n + i], h0->pstream));
     }
-    CK(h0, cudaEventRecord(ev_prep[q % kBatchEv], h0->pstream));
-    CK(h0, cudaStreamWaitEvent(s, ev_prep[q % kBatchEv], 0));
-    if (bp.total[q] > 0)
-      CK(h0, launch_forward_batch<T>(reinterpret_cast<const FwdArgs<T> *>(bp.args.p) + (size_t)q * n,
-                                     reinterpret_cast<const int *>(bp.prefix.p) + (size_t)q * (n + 1),
-                                     n, bp.total[q], reinterpret_cast<int *>(bp.counter.p) + q,
-                                     bp.cfg, std::min(bp.ctas, bp.total[q]), s));
-    CK(h0, cudaEventRecord(ev_scat[q % kBatchEv], s));
+    for (int i : order) {
+      if (r * bp.R >= bp.nseg[i]) continue;
+      cudaStream_t ls = lane[k++ & 1];
+      CK(h0, cudaStreamWaitEvent(ls, ev_prep[r * n + i], 0));
+      CK(h0, launch_forward<T>(prm[r].a[i], c.pipe ? prm[r].tm[i].b : nullptr, bp.cfg, ls));
+      CK(h0, cudaEventRecord(ev_scat[r * n + i], ls));
+    }
   }
-  CK(h0, cudaEventRecord(ev[1], h0->pstream));
+  // join: every prep precedes a scatter, and the second lane joins `s`
+  CK(h0, cudaEventRecord(ev[1], h0->bstream));
   CK(h0, cudaStreamWaitEvent(s, ev[1], 0));
   return FWH_OK;
 }
@@ -1317,11 +1391,12 @@ extern "C" fwh_status fwh_batch_forward(int n, const fwh_handle *hs, const void 
     fwh_status st = prepare_window(h, nt[i]);
     if (st != FWH_OK) return fail(h0, st, h->err);
   }
-  {  // series buffers (a ring of time segments for long records) before the key
+  {  // series buffers (the whole record, or a ring of time segments) before the key
     const FwdConfig c = fwd_config(h0->precision == FWH_FP64, batch_cfg(n, hs, h0));
     const int seg = c.seg_chunks * 32 * c.tk;
+    const int R = batch_round_segs(h0, seg);
     for (int i = 0; i < n; ++i)
-      CK(h0, ensure(hs[i]->X, (size_t)hs[i]->P * batch_x_ld(hs[i], seg) * kRec *
+      CK(h0, ensure(hs[i]->X, (size_t)hs[i]->P * batch_x_ld(hs[i], seg, R) * kRec *
                                   tsize(h0->precision)));
   }
   std::vector<uintptr_t> key;
@@ -1340,15 +1415,12 @@ extern "C" fwh_status fwh_batch_forward(int n, const fwh_handle *hs, const void 
   key.push_back((uintptr_t)(h0->cfg + 1));
   key.push_back((uintptr_t)h0->wait_limit);
   key.push_back((uintptr_t)h0->withhold);
+  key.push_back((uintptr_t)h0->batch_ring);
+  key.push_back((uintptr_t)h0->batch_form);
   if (!h0->side) {
     CK(h0, cudaStreamCreateWithFlags(&h0->side, cudaStreamNonBlocking));
     CK(h0, cudaEventCreateWithFlags(&h0->bev[0], cudaEventDisableTiming));
     CK(h0, cudaEventCreateWithFlags(&h0->bev[1], cudaEventDisableTiming));
-  }
-  {
-    fwh_status st0 = ensure_pstream(h0);
-    if (st0 == FWH_OK) st0 = ensure_events(h0, 2 + 2 * kBatchEv);
-    if (st0 != FWH_OK) return st0;
   }
   auto it = h0->graphs.find(key);
   if (it == h0->graphs.end()) {

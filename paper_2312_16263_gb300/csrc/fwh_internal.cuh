@@ -188,15 +188,25 @@ cudaError_t launch_plan(T *coef, const int *set_begin, int nsets, int O, int sla
                         int half_bytes, int slot_bytes, int *i0max_tab, int *err,
                         cudaStream_t s);
 
-// Batched persistent forward.
-template <typename T>
-struct BatchItemDesc {
-  FwdArgs<T> args;          // per-surface arguments
-  int items;                // work items of this surface
+// Batched persistent forward: the arguments of one launch, passed by value
+// as a __grid_constant__ kernel parameter (under 9 KB at kMaxBatchSurf
+// surfaces), so that the kernel reads them from the constant bank and hands
+// the descriptors' parameter-space addresses to its tensor copies.
+struct alignas(64) TmapBytes {
+  unsigned char b[128];   // a CUtensorMap (encoded by encode_x_tensor_map)
 };
 template <typename T>
-cudaError_t launch_forward_batch(const FwdArgs<T> *d_args, const int *d_item_prefix,
-                                 int n_surf, int total_items, int *d_counter,
-                                 int cfg_idx, int n_ctas, cudaStream_t s);
+struct alignas(64) BatchParams {
+  TmapBytes tm[kMaxBatchSurf];      // X descriptor of each surface
+  FwdArgs<T> a[kMaxBatchSurf];      // arguments of each surface (tmX unused)
+  int prefix[kMaxBatchSurf + 1];    // first work item of each surface; [n_surf] = total
+  int n_surf, total;
+};
+template <typename T>
+cudaError_t launch_forward_batch(const BatchParams<T> &params, int *d_counter, int cfg_idx,
+                                 int n_ctas, cudaStream_t s);
+// The same work items as one ordinary grid (one CTA per item, no queue).
+template <typename T>
+cudaError_t launch_forward_multi(const BatchParams<T> &params, int cfg_idx, cudaStream_t s);
 
 }  // namespace fwh

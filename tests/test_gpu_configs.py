@@ -6,8 +6,9 @@
   loss = sum p_out^2 against central differences of the same loss taken
   through the oracle's forward on 64 random (panel, time, field) entries,
   each entry above a floor held to a relative bound;
-* the eight uneven surfaces of the batched form, scaled down, through one
-  persistent launch, against the oracle and against one call per surface.
+* the eight uneven surfaces of the batched form, at full size and scaled
+  down, whole-record and streamed through rings of time segments, against the
+  oracle and against one call per surface.
 """
 import os
 
@@ -140,8 +141,10 @@ def _host_bytes_free():
 @pytest.mark.parametrize("prec", ["mixed"])
 def test_batched_eight_surfaces_full_size(dev, prec):
     """The eight uneven surfaces at full size (524288 panels, 4096 steps, 1024
-    observers each): one graph of per-segment persistent launches streaming
-    the series through a two-segment ring, checked against the oracle on two
+    observers each): whole records in the pipelined form; the same streamed
+    through a ring of two 512-sample segments (four rounds), as one grid and
+    as the persistent work-queue kernel, each equal to the first to the
+    rounding of the output sums; the first checked against the oracle on two
     observers of every surface (rel-L2 per observer at the mixed bar) and
     against one fwh_forward call per surface."""
     from paper_2312_16263_gb300 import FWH, batch_forward
@@ -152,6 +155,13 @@ def test_batched_eight_surfaces_full_size(dev, prec):
     outs = batch_forward(surfs, fields)
     outs = batch_forward(surfs, fields)      # the replayed graph
     surfs[0].check()
+    for ring, form in ((1024, "pipelined"), (0, "grid"), (0, "persistent")):
+        surfs[0].set_batch_options(ring, form)
+        other = batch_forward(surfs, fields)
+        surfs[0].check()
+        for a, b in zip(other, outs):
+            torch.testing.assert_close(a, b, rtol=1e-12, atol=1e-12 * b.abs().max().item())
+        del other
     free = _host_bytes_free()
     for w, s, f, p in zip(ws, surfs, fields, outs):
         _, nv = s.window(w.nt)
@@ -169,12 +179,21 @@ def test_batched_eight_surfaces_full_size(dev, prec):
     del outs
 
 
-def test_batched_uneven_surfaces(dev):
+@pytest.mark.parametrize("ring,form", [(0, "pipelined"), (512, "pipelined"),
+                                       (1536, "pipelined"), (0, "grid"), (1536, "grid"),
+                                       (0, "persistent"), (1536, "persistent")])
+def test_batched_uneven_surfaces(dev, ring, form):
+    """The eight surfaces at 1/64 scale (2048 steps, four 512-sample
+    segments): whole records in one launch, a one-segment ring (four rounds)
+    and a three-segment ring (a full round and a one-segment round), in each
+    launch form, each against one fwh_forward call per surface and the
+    oracle."""
     from paper_2312_16263_gb300 import FWH, batch_forward
     ws = batch_workloads(scale=1 / 64, nt=32768)  # 2048 steps: every window non-empty
     surfs = [FWH.from_workload(w, "mixed") for w in ws]
     fields = [w.fields(device=dev, dtype="float32") for w in ws]
     singles = [s.forward(f).clone() for s, f in zip(surfs, fields)]
+    surfs[0].set_batch_options(ring, form)
     for _ in range(2):  # the second call replays the captured graph
         outs = batch_forward(surfs, fields)
         for a, b in zip(outs, singles):

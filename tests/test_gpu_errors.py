@@ -116,5 +116,37 @@ def test_timeout_reaches_autograd(dev):
     s.close()
 
 
+def test_timeout_in_batched_call(dev):
+    """Batched calls under withheld copies (every launch form, whole records
+    and a ring): each compute warp gives up on its first stage (the
+    persistent producer also ends its item queue), the timeout
+    reaches fwh_check of the leading handle, and the same handles give correct
+    results afterwards."""
+    from paper_2312_16263_gb300 import FWH, _abi, batch_forward
+    ws, surfs, fields = [], [], []
+    for scale in (0.5, 0.25):
+        w = workload(1, scale=scale)
+        w.nt = 1200
+        ws.append(w)
+        surfs.append(FWH.from_workload(w, "mixed"))
+        fields.append(w.fields(device=dev, dtype="float32"))
+    singles = [sx.forward(fx).clone() for sx, fx in zip(surfs, fields)]
+    for ring, form in ((0, "pipelined"), (512, "pipelined"), (0, "grid"), (0, "persistent"),
+                       (512, "persistent")):
+        surfs[0].set_batch_options(ring, form)
+        surfs[0].set_wait_limit(2000, withhold_copies=True)
+        batch_forward(surfs, fields)
+        st = surfs[0].lib.fwh_check(surfs[0].h, _abi_stream())
+        assert st == _abi.FWH_ERR_TIMEOUT, st
+        surfs[0].set_wait_limit(0)
+        outs = batch_forward(surfs, fields)
+        surfs[0].check()
+        for a, b in zip(outs, singles):
+            torch.testing.assert_close(a, b, rtol=1e-12, atol=1e-12 * b.abs().max().item())
+    _assert_matches_oracle(ws[1], surfs[1], fields[1], outs[1])
+    for sx in surfs:
+        sx.close()
+
+
 def _abi_stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
