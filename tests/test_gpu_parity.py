@@ -164,7 +164,7 @@ def test_host_pointer_path_matches_device(dev, prec):
     assert torch.allclose(p_host, p_dev, rtol=0, atol=1e-14 * p_dev.abs().max().item())
 
 
-@pytest.mark.parametrize("cfg", [0, 5])
+@pytest.mark.parametrize("cfg", [0, 5, 11])
 def test_host_slab_pipeline_matches_device(dev, cfg):
     """Host FP32 fields of 256 frames or more are copied in 128-frame slabs,
     each slab's series prepared once the next has landed and each two-chunk
@@ -174,8 +174,11 @@ def test_host_slab_pipeline_matches_device(dev, cfg):
     slab and below-threshold record lengths, from pinned and pageable memory,
     with a device output too.  The series are the same bits either way; the
     shorter scatter segments split the FP32 per-bin partial sums at segment
-    boundaries differently, so the outputs agree to FP32 rounding (1e-5
-    relative L2 per observer; stale or missing series would be O(1))."""
+    boundaries differently, so the outputs agree to the rounding of those
+    sums: at most 1e-6 relative L2 per observer with plain FP32 window sums
+    (2.9e-7 measured on a GB300) and 1e-7 with the compensated sums of shape
+    11 (1.5e-8 measured); stale or missing series would be O(1)."""
+    tol = 1e-7 if cfg == 11 else 1e-6
     w = workload(4)
     from paper_2312_16263_gb300 import FWH
     s = FWH.from_workload(w, "mixed")
@@ -194,7 +197,7 @@ def test_host_slab_pipeline_matches_device(dev, cfg):
         for src in (f, f.pin_memory()):
             p_host = s.forward(src)
             assert p_host.device.type == "cpu"
-            assert rel(p_host, p_dev) <= 1e-5, nt
+            assert rel(p_host, p_dev) <= tol, nt
             # bins past each observer's window stay exactly zero
             for o, n in enumerate(nv):
                 assert torch.all(p_host[o, int(n):] == 0), (nt, o)
@@ -203,7 +206,7 @@ def test_host_slab_pipeline_matches_device(dev, cfg):
         out = torch.empty((s.O, nt), dtype=torch.float64, device=dev)
         f_pinned = f.pin_memory()
         s.forward(f_pinned, out)
-        assert rel(out.cpu(), p_dev) <= 1e-5, nt
+        assert rel(out.cpu(), p_dev) <= tol, nt
         del f_pinned
 
 
