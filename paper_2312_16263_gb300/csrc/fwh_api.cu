@@ -1139,14 +1139,14 @@ void fwh_destroy(fwh_handle h) {
 // scatter launches) is captured in a CUDA graph and replayed.
 //
 // The record is cut into rounds of R consecutive time segments.  By default
-// one round holds the whole record: the series of every surface are prepared
-// first and ONE launch scatters every work item of every surface.  With a
-// ring (fwh_set_batch_options), X keeps R segments per surface and the rounds
-// alternate prep and scatter.  Within a round the work items run in the order
-// (surface, panel set, segment, observer group), so the CTAs in flight at any
-// moment share a few panel sets' coefficient records and X rows in L2.  The
-// scatter launch is one grid with a CTA per item (default) or the persistent
-// work-queue kernel with one CTA per SM slot.
+// one round holds the whole record; with a ring (fwh_set_batch_options), X
+// keeps R segments per surface and each round prepares and scatters its
+// segments.  Within a round the work items run in the order (surface, panel
+// set, segment, observer group), so the CTAs in flight at any moment share a
+// few panel sets' coefficient records and X rows in L2.  A round's scatter is
+// one launch per surface (FWH_BATCH_PIPELINED, the default), one grid with a
+// CTA per item over every surface (FWH_BATCH_GRID), or the persistent
+// work-queue kernel with one CTA per SM slot (FWH_BATCH_PERSISTENT).
 // ---------------------------------------------------------------------------
 namespace {
 

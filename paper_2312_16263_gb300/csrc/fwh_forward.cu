@@ -171,10 +171,10 @@ __device__ __forceinline__ unsigned suspend_for(long long limit) {
 }
 // Bounded wait: false on timeout (flag raised) or when another warp aborted.
 // `limit` is the bound in SM clocks (<= 0: kWaitCycles).  The first test uses
-// a fixed suspend hint, so that it does not wait on `limit` and `err` (which
-// the persistent kernel keeps in shared memory): on the usual path, where
-// the phase is already complete, neither is read.  A bound shorter than the
-// hint runs out after the hint instead (a test-only case).
+// a fixed suspend hint, so that it does not wait on the loads of `limit` and
+// `err`: on the usual path, where the phase is already complete, neither is
+// needed.  A bound shorter than the hint runs out after the hint instead (a
+// test-only case).
 constexpr unsigned kFirstSuspendNs = 1000;
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int *err,
                                           volatile int *abort, long long limit = 0) {
@@ -474,8 +474,9 @@ __device__ __forceinline__ void produce_item(const FwdArgs<T> &a, const Item<T, 
   // Both cursors (the load and the L2 prefetch running ahead of it) advance
   // incrementally: this lane's per-step work stays short, since it is on the
   // critical path of every stage refill.
-  // the item's constants in registers (the persistent kernel's arguments sit
-  // in shared memory, which every copy's memory clobber would make it re-read)
+  // the item's constants in registers (the batched kernels read their
+  // arguments through a pointer, which every copy's memory clobber would make
+  // them re-read)
   const T *const X = a.X;
   const T *const coef = a.coef;
   const int x_ld = a.x_ld, O = a.O;
