@@ -237,20 +237,31 @@ def test_backward_matches_oracle_adjoint(dev, prec, n_obs, npol, naz, nt):
     assert err <= (1e-10 if prec == "fp64" else 1e-4), err
 
 
-def test_batch_forward_matches_single(dev):
+@pytest.mark.parametrize("ring", [0, 512])
+@pytest.mark.parametrize("form", ["pipelined", "grid", "persistent"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_forward_matches_single(dev, prec, form, ring):
+    """Three small surfaces (one record of three 512-sample segments) in one
+    batched call, in every launch form, with whole records and with a
+    one-segment ring (three rounds), equal to one fwh_forward call per
+    surface to the rounding of the output sums.  FP64 runs the direct-load
+    shape with whole records and the copy-pipeline shape with the ring."""
     from paper_2312_16263_gb300 import FWH, batch_forward
     rng = np.random.default_rng(11)
     surfs, fields, singles = [], [], []
-    for i, (npol, naz, nt, no) in enumerate([(8, 16, 200, 5), (13, 7, 131, 9), (20, 40, 390, 3)]):
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    cfg = 1 if (prec == "fp64" and ring) else -1
+    for i, (npol, naz, nt, no) in enumerate([(8, 16, 200, 5), (13, 7, 131, 9), (20, 40, 1100, 3)]):
         sf = uv_sphere(1.0 + 0.3 * i, npol, naz, center=(i, 0, 0))
         obs = observers_circle(30.0, no) + rng.normal(size=(no, 3))
-        s = FWH(sf.centroids, sf.normals, sf.areas, 0.3 + 0.1 * i, 0.1 * i, 0.02, "mixed",
+        s = FWH(sf.centroids, sf.normals, sf.areas, 0.3 + 0.1 * i, 0.1 * i, 0.02, prec,
                 observers=obs)
-        f = torch.as_tensor(rng.normal(size=(nt, 5, sf.n_panels)) * 1e-3,
-                            dtype=torch.float32, device=dev)
+        s.set_tile_config(cfg)
+        f = torch.as_tensor(rng.normal(size=(nt, 5, sf.n_panels)) * 1e-3, dtype=dtype, device=dev)
         surfs.append(s)
         fields.append(f)
         singles.append(s.forward(f).clone())
+    surfs[0].set_batch_options(ring, form)
     for _ in range(2):  # second call replays the captured graph
         outs = batch_forward(surfs, fields)
         for a, b in zip(outs, singles):
