@@ -309,7 +309,13 @@ def extra_legs(dev):
     w = workload(1)
     f = w.fields(device=dev, dtype="float64")
     p_ref, nv_ref, orate, thr = _oracle_leg(w, f.cpu().numpy(), np.arange(w.observers.shape[0]))
-    leg = {"workload": w.name, "evals": w.evals, "oracle_evals_per_s": orate, "oracle_cores": thr}
+    # the same on one host core
+    from oracle import Oracle
+    t0 = time.perf_counter()
+    Oracle.from_workload(w).forward(f.cpu().numpy(), w.observers, threads=1)
+    orate1 = w.evals / (time.perf_counter() - t0)
+    leg = {"workload": w.name, "evals": w.evals, "oracle_evals_per_s": orate, "oracle_cores": thr,
+           "oracle_evals_per_s_1core": orate1}
     for prec in ("fp64", "mixed"):
         s = FWH.from_workload(w, prec)
         fx = f if prec == "fp64" else f.float()
