@@ -322,7 +322,13 @@ def extra_legs(dev):
         o = torch.empty((s.O, w.nt), dtype=torch.float64, device=dev)
         ms = _time_calls(lambda: s.forward(fx, o), 20)
         _, nv = s.window(w.nt)
+        # few observers: the series bytes per call (one row per panel and
+        # sample per observer group; 64 B mixed, 128 B FP64) against HBM too
+        groups = -(-w.observers.shape[0] // 36)
+        xbytes = (64 if prec == "mixed" else 128) * w.surface.n_panels * w.nt * groups
         leg[prec] = {"ms": ms, "evals_per_s": w.evals / (ms / 1e3),
+                     "series_bytes": xbytes,
+                     "hbm_frac": xbytes / (ms / 1e3) / 1e9 / hbm_peak_gbs()[0],
                      "rel_l2_vs_oracle": rel_l2_stats(o.cpu().numpy(), nv, p_ref, nv_ref,
                                                       np.arange(w.observers.shape[0]))}
         s.check()
