@@ -269,6 +269,21 @@ def test_batch_forward_matches_single(dev, prec, form, ring):
     surfs[0].check()
 
 
+def test_batch_options_rejected(dev):
+    """A negative ring length or an unknown launch form is refused with
+    FWH_ERR_ARG and leaves the options as they were."""
+    from paper_2312_16263_gb300 import FWH, _abi
+    sf = uv_sphere(1.0, 8, 16)
+    s = FWH(sf.centroids, sf.normals, sf.areas, 0.3, 0.0, 0.02, "mixed",
+            observers=observers_circle(30.0, 4))
+    assert s.lib.fwh_set_batch_options(s.h, -1, _abi.FWH_BATCH_GRID) == _abi.FWH_ERR_ARG
+    assert s.lib.fwh_set_batch_options(s.h, 0, 3) == _abi.FWH_ERR_ARG
+    assert s.lib.fwh_set_batch_options(s.h, 512, _abi.FWH_BATCH_PERSISTENT) == _abi.FWH_OK
+    with pytest.raises(KeyError):
+        s.set_batch_options(0, "queue")
+    s.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_every_tile_config_agrees(dev, prec):
     """Every forward tile configuration (direct-load and TMA-pipeline kernels)
