@@ -335,11 +335,20 @@ fwh_status fwh_psd(int64_t n_sig, const double *p, int64_t ld, const int64_t *n_
  * of the last frame's, N_o = floor((t_end - t_start) / dt) + 1.  Each panel's
  * signal and arrival time are natural cubic splines over tau; bin j takes the
  * signal at the tau* whose arrival is t_j.  The motion must stay subsonic
- * (|M_r| < 1).  Device scratch of up to about 2 GiB is taken with
- * cudaMallocAsync on `stream`; the call synchronises.
+ * (|M_r| < 1).  Device scratch of 32 nt P bytes per observer, up to
+ * the budget of fwh_set_moving_scratch (16 GiB by default; observers are
+ * split over launches that fit it, at least one observer per launch), is
+ * taken with cudaMallocAsync on `stream`; the call synchronises.
  * Errors: FWH_ERR_ARG (sizes, |w| >= c0, non-positive c0, rho0, dt),
  * FWH_ERR_OOM / FWH_ERR_CUDA (message via fwh_last_error(NULL)).
  */
+/*
+ * Scratch budget in bytes of later fwh_forward_moving calls, process-wide
+ * (0 restores the default of 16 GiB).  Smaller budgets split the observers
+ * over more, smaller launches.  Errors: FWH_ERR_ARG for a negative budget.
+ */
+fwh_status fwh_set_moving_scratch(int64_t bytes);
+
 fwh_status fwh_forward_moving(int64_t n_panels, int64_t nt, const double *y,
                               const double *normals, const double *velocities,
                               const double *areas, double c0, double rho0, double dt,

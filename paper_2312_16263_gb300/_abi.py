@@ -51,6 +51,7 @@ SIGNATURES = {
     "fwh_forward_moving": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, _vp, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, _vp, _i64, _vp,
                                           _vp, _vp, _dp, _ip64, _vp]),
+    "fwh_set_moving_scratch": (ctypes.c_int, [_i64]),
     "fwh_psd": (ctypes.c_int, [_i64, _vp, _i64, _vp, ctypes.c_double, _i64, ctypes.c_int,
                                ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "fwh_get_sizes": (ctypes.c_int, [_vp, _ip64, _ip64, ctypes.POINTER(ctypes.c_int)]),

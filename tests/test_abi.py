@@ -83,6 +83,7 @@ def test_argument_validation_without_gpu(lib):
     assert lib.fwh_backward(None, P(1), 10, P(1), P(1), None) == _abi.FWH_ERR_ARG
     assert lib.fwh_batch_forward(0, None, None, None, None, None) == _abi.FWH_ERR_ARG
     assert lib.fwh_set_batch_options(None, 0, _abi.FWH_BATCH_GRID) == _abi.FWH_ERR_ARG
+    assert lib.fwh_set_moving_scratch(-1) == _abi.FWH_ERR_ARG
     lib.fwh_destroy(None)
     assert lib.fwh_version().startswith(b"fwh-gb300")
 

@@ -116,10 +116,17 @@ def test_moving_spheres_match_oracle(dev, motion, n_pol, n_az, nt, n_obs):
 
 def test_observers_split_over_launches(dev):
     """4 x nt x P FP64 scratch columns per observer (1 GiB here) fit two
-    observers in the 2 GiB budget, so the three observers take two launches."""
+    observers in a 2 GiB budget, so the three observers take two launches."""
     import sys, os
     sys.path.insert(0, os.path.dirname(__file__))
+    from paper_2312_16263_gb300 import _abi
+    lib = _abi.load()
     y, n, v, dS, f = _sphere("spin", 64, 128, 4096, 0.02)     # 8192 panels
     assert 3 * (4 * 4096 * 8192 * 8) > 2 << 30
     obs = observers_circle(15.0, 3)
-    _run(dev, y, n, v, dS, 1.0, 1.0, 0.02, f, obs, np.zeros(3))
+    assert lib.fwh_set_moving_scratch(-1) == _abi.FWH_ERR_ARG
+    _abi.check(lib.fwh_set_moving_scratch(2 << 30), None)
+    try:
+        _run(dev, y, n, v, dS, 1.0, 1.0, 0.02, f, obs, np.zeros(3))
+    finally:
+        _abi.check(lib.fwh_set_moving_scratch(0), None)
