@@ -69,6 +69,10 @@ def parse_args():
     ap.add_argument("--profile-backward", action="store_true",
                     help="small case for ncu: the 16384-panel x 1024-step x 36-observer dipole, "
                          "two forward + backward calls")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="small case for ncu: one contour surface of the eight-surface set "
+                         "(16384 panels x 2048 steps x 1024 observers) through fwh_forward, "
+                         "the single-grid and the persistent batched forms, twice each")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--tile-config", type=int, default=-1,
                     help="forward tile configuration index (-1: the library default)")
@@ -547,6 +551,33 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def profile_batch(args):
+    """fwh_forward, then a batch of that one surface as one grid and as the
+    persistent work queue (same items, same kernel code), twice each in that
+    order (about 4 GB on the device): the capture target for comparing the
+    three launches (k_forward* launches 4 to 6 are the second round)."""
+    import torch
+    from __graft_entry__ import build
+    build()
+    from fwh_inputs import batch_workloads
+    from paper_2312_16263_gb300 import FWH, batch_forward
+    w = batch_workloads(scale=0.25, nt=2048)[1]
+    s = FWH.from_workload(w, "mixed")
+    f = w.fields(device="cuda:0", dtype="float32")
+    out = torch.empty((s.O, w.nt), dtype=torch.float64, device="cuda:0")
+    res = {}
+    for _ in range(2):
+        s.forward(f, out)
+        for form in ("grid", "persistent"):
+            s.set_batch_options(0, form)
+            res[form] = batch_forward([s], [f])[0]
+    torch.cuda.synchronize()
+    s.check()
+    print(json.dumps({"profile_batch": w.name, "P": w.surface.n_panels, "nt": w.nt,
+                      "O": int(s.O), "max_diff": max(float((r - out).abs().max())
+                                                     for r in res.values())}))
+
+
 def main():
     args = parse_args()
     if args.profile_backward:
@@ -554,6 +585,9 @@ def main():
         return
     if args.profile_case:
         profile_case(args)
+        return
+    if args.profile_batch:
+        profile_batch(args)
         return
     ws, rank, local = dist_setup()
     if args.impl == "reference":
