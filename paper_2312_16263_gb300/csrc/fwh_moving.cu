@@ -21,7 +21,7 @@
 //    times bracket it, tau* solves t(tau*) = t_j there by Newton's method on
 //    the spline of t (three steps from the linear estimate reach FP64
 //    rounding for subsonic motion), and the spline of g at tau* is reduced
-//    over the CTA's panels before one FP64 atomic per bin.
+//    over each warp's panels before one FP64 atomic per warp and bin.
 // Scratch: four FP64 columns of nt per (panel, observer) of a launch; the
 // host splits the observers into launches that fit the scratch budget (16 GiB
 // by default: a budget of 2 GiB, four observers per launch on the 8192-panel
@@ -262,8 +262,8 @@ __global__ void __launch_bounds__(kMTile, 8) k_mscatter(MovArgs a) {
     spline_moments(G, MG, ld, a.nt, a.dt, ipiv);
     spline_moments(TT, MT, ld, a.nt, a.dt, ipiv);
   }
-  // observer bins: every thread walks the same j, the CTA sums its panels
-  __shared__ double red[kMTile / 32];
+  // observer bins: every thread walks the same j, each warp sums its panels
+  // and adds them with one atomic (no CTA barrier per bin)
   const int nv = a.nv[o];
   const double ts = a.ts[o], h = a.dt, h26 = a.dt * a.dt / 6.0;
   int k = 0;
@@ -289,14 +289,7 @@ __global__ void __launch_bounds__(kMTile, 8) k_mscatter(MovArgs a) {
           ((A * A * A - A) * MG[(long)k * ld] + (B * B * B - B) * MG[(long)(k + 1) * ld]) * h26;
     }
     for (int off = 16; off > 0; off >>= 1) val += __shfl_xor_sync(0xffffffffu, val, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = val;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int q = 0; q < kMTile / 32; ++q) s += red[q];
-      atomicAdd(a.p_out + (size_t)o * a.nt + j, s);
-    }
-    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicAdd(a.p_out + (size_t)o * a.nt + j, val);
   }
 }
 
