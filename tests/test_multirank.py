@@ -94,7 +94,15 @@ def test_reference_arm_under_torchrun_prints_once(tmp_path):
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["n_gpus"] == 2
-    assert d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
+    # the reference arm carries the contract keys of the line it stands beside
+    for k in ("metric", "unit", "higher_is_better", "steps", "warmup", "config"):
+        assert k in d, k
+    assert d["higher_is_better"] is True and d["unit"] == "evals/s"
+    assert d["config"]["workload"] == "sphere-dipole-32768x2048x72"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
 
 
 # ---- panel sharding (Sec. III A Face partition, Sec. III B max/min all-reduce) ----
