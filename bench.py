@@ -739,7 +739,11 @@ def main():
     if rank == 0 and ws == 1 and not args.no_extra:
         del fh, oh
         torch.cuda.empty_cache()
-        line.update(extra_legs(dev))
+        try:
+            line.update(extra_legs(dev))
+        except Exception as e:  # the extra keys never cost the headline line
+            line["extra_legs_error"] = f"{type(e).__name__}: {e}"[:500]
+            torch.cuda.empty_cache()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, (pick, p_ref, nv_ref) = cpu_baseline(w)
         line["cpu_baseline"] = cb
